@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the block r1-sparse Jacobian hot path; prints ONE JSON line.
+
+One step is one pass of the whole path over the 128 x 128, N = 60 (b = 63)
+workload, FP64, inputs resident in HBM:
+  update_values (repack S, U, V)  -> SMW block-Jacobi setup
+  -> OPS x matvec y = J x         -> OPS x block-Jacobi apply z = M x
+  -> one J^T x and one M^T x      -> GMRES(30) to 1e-10 (FP64)
+  -> flexible GMRES(30) to 1e-10 with FP32 operators (mixed)
+  -> adjoint GMRES on J^T and the gradient outer products.
+``value`` = FP64 matvecs + FP64 block-Jacobi applies executed in a step (the
+explicit loops plus those inside the FP64 and adjoint solves) / step time.
+FP32 operator calls of the mixed solve are not counted.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun) every rank runs an independent replica of the same
+workload on its own GPU (no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian matvecs/s + block-Jacobi applies/s (HBM % peak) vs dense BSR, same GPU"
+UNIT = "ops/s"
+WORKLOAD = "grid128_N60"
+N_SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2          # GB300: measured 0.594 T FMA/s at 1.98 GHz on 152 SMs
+L2_BYTES = 135528448
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def _traffic_record():
+    """ncu DRAM bytes per sts_jac_matvec call, valid only for the kernel source it was taken on."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_grid128_N60.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            rec[k.strip()] = v.strip()
+    src = open(os.path.join(ROOT, "paper_2403_09198_gb300", "csrc", "kernels_matvec.cu"), "rb").read()
+    if rec.get("kernels_matvec_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return float(rec["dram_bytes_per_matvec"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(w, n_ops: int):
+    """Time the FP64 oracle (as it stands) on the host cores: n_ops matvecs and
+    n_ops block-Jacobi applies of the same workload, factors set up untimed."""
+    import numpy as np
+    import oracle
+    J = oracle.Jacobian.from_workload(w)
+    F = oracle.bj_setup(J)
+    x = np.random.default_rng(0).standard_normal(w.n)
+    t0 = time.perf_counter()
+    for _ in range(n_ops):
+        oracle.matvec(J, x)
+        oracle.bj_apply(F, x)
+    dt = time.perf_counter() - t0
+    return 2 * n_ops / dt, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, same metric and unit."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2403_09198_gb300 import inputs
+    oracle.build()
+    w = inputs.named_workload(WORKLOAD)
+    import numpy as np
+    J = oracle.Jacobian.from_workload(w)
+    F = oracle.bj_setup(J)
+    x = np.random.default_rng(0).standard_normal(w.n)
+
+    def step():
+        oracle.matvec(J, x)
+        oracle.bj_apply(F, x)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = 2 * args.steps / dt
+    sample = (f"per step 1 dense-block matvec + 1 dense-LU block-Jacobi apply of {WORKLOAD} "
+              f"(factors set up once, untimed)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(w):
+    return {"workload": f"{WORKLOAD}: 128x128 cells, N=60 levels, b=63, band +-2, "
+                        f"2 pairs per diagonal block, 1 per neighbour block, seed 1",
+            "n_cells": w.n_cells, "N": w.N, "b": w.b, "nnz_S": int(w.S.shape[0]),
+            "n_pairs": w.n_pairs, "l2": "inputs larger than L2 (425 MB per matvec, 137 MB per apply)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2403_09198_gb300 import binding, inputs
+    from paper_2403_09198_gb300.binding import StsJacobian
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    __graft_entry__.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = inputs.named_workload(WORKLOAD)
+    n = w.n
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    S, U, V, b, Wd = t(w.S), t(w.U), t(w.V), t(w.rhs), t(w.W)
+    # component-major vectors for the explicit loops (the kernels' own layout)
+    jac = StsJacobian(w, S, U, V, layout="component", transpose=True, mixed=True)
+    stream = torch.cuda.current_stream()
+    xv = torch.randn(n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(xv)
+    z = torch.empty_like(xv)
+    ops = args.ops
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    per = {"mv": [], "ap": []}
+    counted = {}
+
+    def step(record=False):
+        jac.update_values(S, U, V)
+        jac.bjacobi_setup()
+        ev[0].record(stream)
+        for _ in range(ops):
+            jac.matvec(xv, out=y)
+        ev[1].record(stream)
+        for _ in range(ops):
+            jac.bjacobi_apply(xv, out=z)
+        ev[2].record(stream)
+        jac.matvec(xv, out=y, trans=True)
+        jac.bjacobi_apply(xv, out=z, trans=True)
+        xs, i64 = jac.gmres(b, rtol=1e-10, restart=30)
+        xm, imx = jac.gmres(b, rtol=1e-10, restart=30, mixed=True)
+        lam, iad = jac.gmres(Wd * Wd * xs, rtol=1e-10, restart=30, trans=True)
+        g = jac.grad(lam, xs)
+        if record:
+            torch.cuda.synchronize()
+            per["mv"].append(ev[0].elapsed_time(ev[1]) / ops)
+            per["ap"].append(ev[1].elapsed_time(ev[2]) / ops)
+        # FP64 operator calls of the step: explicit loops, one J^T and one M^T,
+        # and per FP64 solve (iterations + restarts + 1) matvecs and iterations applies
+        mv = ops + 1 + (i64.iterations + i64.restarts + 1) + (iad.iterations + iad.restarts + 1) \
+            + (imx.restarts + 1)
+        ap = ops + 1 + i64.iterations + iad.iterations
+        counted.update(mv=mv, ap=ap, gmres=i64, mixed=imx, adjoint=iad)
+        return xs, xm, lam, g
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = binding.launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ops_done = 0
+    for k in range(args.steps):
+        step(record=True)
+        ops_done += counted["mv"] + counted["ap"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = binding.launch_count() - l0
+    ck = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = ops_done * ws / elapsed
+    mv_ms = statistics.median(per["mv"])
+    ap_ms = statistics.median(per["ap"])
+
+    # roofline of the dominant operation (one sts_jac_matvec = pair-dot pass + main pass)
+    hbm_peak, sm_max_mhz, peak_kind = _peaks()
+    mv_bytes = 8 * (w.S.shape[0] + 2 * w.n_pairs * w.b + 2 * n) + 4 * w.nnzb
+    mv_flops = 2 * (w.S.shape[0] + 2 * w.n_pairs * w.b)
+    fp64_peak = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
+    ach_tflops = mv_flops / (mv_ms * 1e-3) / 1e12
+    ap_bytes = 8 * (w.n_cells * (w.nnz_d + 2 * w.r_diag * w.b + w.r_diag ** 2) + 2 * n)
+
+    # end to end through the public API: values and vectors from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hS = torch.from_numpy(w.S).pin_memory()
+        hU = torch.from_numpy(np.ascontiguousarray(w.U)).pin_memory()
+        hV = torch.from_numpy(np.ascontiguousarray(w.V)).pin_memory()
+        hx = xv.cpu().pin_memory()
+        hb = torch.from_numpy(w.rhs).pin_memory()
+        hW = torch.from_numpy(w.W).pin_memory()
+        outs = None
+
+        def e2e_step():
+            nonlocal outs
+            jac.update_values(hS.numpy(), hU.numpy(), hV.numpy())
+            xv.copy_(hx, non_blocking=True)
+            b.copy_(hb, non_blocking=True)
+            Wd.copy_(hW, non_blocking=True)
+            xs, xm, lam, g = step()
+            outs = [y.cpu(), z.cpu(), xs.cpu(), xm.cpu(), lam.cpu()] + [a.cpu() for a in g]
+            return outs
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_ops = 0
+        n_e2e = max(1, min(args.steps, 5))
+        for _ in range(n_e2e):
+            e2e_step()
+            e2e_ops += counted["mv"] + counted["ap"]
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        h2d = 8 * (w.S.shape[0] + 2 * w.n_pairs * w.b + 3 * n)
+        d2h = sum(a.numel() * a.element_size() for a in outs)
+        e2e = {"value": e2e_ops * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e / n_e2e}
+
+    # dense-BSR baseline on the same GPU (outside the timed step)
+    dense = None
+    if not args.no_dense:
+        jd = StsJacobian(w, S, U, V, layout="component", dense=True)
+
+        def avg(fn, reps):
+            for _ in range(2):
+                fn()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            c.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(c) / reps
+
+        dmv = avg(lambda: jd.matvec(xv, out=y), 10)
+        t0 = time.perf_counter()
+        jd.bjacobi_setup()
+        dsetup = time.perf_counter() - t0
+        dap = avg(lambda: jd.bjacobi_apply(xv, out=z), 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, dinfo = jd.gmres(b, rtol=1e-10, restart=30)
+        dgm = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jac.bjacobi_setup()
+        fsetup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, finfo = jac.gmres(b, rtol=1e-10, restart=30)
+        fgm = time.perf_counter() - t0
+        dense_bytes = 8 * (w.nnzb * w.b * w.b + 2 * n)
+        dense = {"matvec_ms": dmv, "apply_ms": dap, "setup_ms": 1e3 * dsetup,
+                 "gmres_ms": 1e3 * dgm, "gmres_iterations": dinfo.iterations,
+                 "gmres_true_rel_residual": dinfo.true_rel_residual,
+                 "matvec_GBps": dense_bytes / (dmv * 1e-3) / 1e9,
+                 "memory_GB": jd.memory_bytes() / 1e9,
+                 "speedup_matvec": dmv / mv_ms, "speedup_apply": dap / ap_ms,
+                 "factored_setup_ms": 1e3 * fsetup, "factored_gmres_ms": 1e3 * fgm,
+                 "factored_gmres_true_rel_residual": finfo.true_rel_residual,
+                 "speedup_gmres_time_to_tolerance": dgm / fgm,
+                 "factored_memory_GB": jac.memory_bytes() / 1e9}
+        jd.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        v, dt, cores = oracle_sample(w, args.cpu_ops)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_ops} dense-block matvecs + {args.cpu_ops} dense-LU block-Jacobi "
+                         f"applies of {WORKLOAD} on the host cores ({dt:.1f} s)"}
+
+    traffic = _traffic_record()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(_config(w), ops_per_step={"matvec_fp64": counted["mv"], "bj_apply_fp64": counted["ap"],
+                                                 "explicit_loops": ops},
+                       parallelism="replicas" if ws > 1 else "single GPU",
+                       vec_layout="component-major"),
+        "roofline": {"bound": "alu", "kernel": "sts_jac_matvec FP64 (k_pair_dots + k_mv_main)",
+                     "achieved": ach_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": ach_tflops / fp64_peak,
+                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_max_mhz:.0f} MHz",
+                     "traffic": traffic, "algorithmic_bytes": mv_bytes,
+                     "hbm": {"achieved": mv_bytes / (mv_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": mv_bytes / (mv_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_kind": peak_kind}},
+        "breakdown": {"matvec_ms": mv_ms, "bj_apply_ms": ap_ms,
+                      "bj_apply_GBps": ap_bytes / (ap_ms * 1e-3) / 1e9,
+                      "gmres_iterations": counted["gmres"].iterations,
+                      "gmres_true_rel_residual": counted["gmres"].true_rel_residual,
+                      "mixed_iterations": counted["mixed"].iterations,
+                      "mixed_restarts": counted["mixed"].restarts,
+                      "mixed_true_rel_residual": counted["mixed"].true_rel_residual,
+                      "adjoint_iterations": counted["adjoint"].iterations},
+        "dense_bsr": dense,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    jac.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ops", type=int, default=1000, help="explicit matvec / apply loop length per step")
+    p.add_argument("--cpu-ops", type=int, default=10)
+    p.add_argument("--no-dense", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    args = p.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

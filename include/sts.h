@@ -1,0 +1,247 @@
+/*
+ * sts.h -- C ABI of the GB300 block r1-sparse Jacobian library (libsts.so).
+ *
+ * The library stores a first-order finite-volume Jacobian the way the paper
+ * does (Gouasmi & Murman, "Sparse Data Structures for Efficient State-to-State
+ * Kinetic Simulations", Sections 4-6): every nonzero block is a sparse matrix
+ * plus a few rank-one pairs,
+ *
+ *     J_ij = S_ij + sum_k u_ijk v_ijk^T                  (Section 4.3, Eq. r1_flux_left/right, r1_chem)
+ *
+ * and offers the Jacobian-vector product (Section 5.2), a block-Jacobi
+ * preconditioner applied through the Sherman-Morrison-Woodbury formula
+ * (Section 6, steps SMW-1..3), restarted right-preconditioned (F)GMRES
+ * (Section 6, Eq. right_precond_system), the transposed operators and the
+ * adjoint outer products used to differentiate x = J^-1 b.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an sts_status; STS_OK (0) on success.  On failure
+ *   sts_last_error() returns a message for the calling thread.  No C++
+ *   exception crosses this boundary.
+ * - Cells are numbered 0..n_cells-1.  The block size b is the number of
+ *   unknowns per cell (b = N + 3 for N quantum levels, two momenta and one
+ *   energy, Section 2.1; any b >= 1 is accepted).
+ * - Vectors have n_cells * b entries.  Their layout is fixed per handle by
+ *   sts_jac_desc.vec_layout: STS_LAYOUT_CELL_MAJOR stores cell c's b values
+ *   contiguously (x[c*b + p]); STS_LAYOUT_COMPONENT_MAJOR stores component p of
+ *   all cells contiguously (x[p*n_cells + c]), the layout the kernels use
+ *   internally, so it avoids two transposes per call.
+ * - "device" pointers are CUDA device (or managed) memory on the current
+ *   device; "host" pointers are ordinary host memory.  The library never takes
+ *   ownership of caller memory; arguments need to stay valid only for the
+ *   duration of the call (asynchronous calls: until the work on the handle's
+ *   stream has finished).
+ * - All GPU work is issued on the stream given at creation.  Calls marked
+ *   "asynchronous" return before the work finishes; the others synchronise
+ *   that stream before returning.
+ * - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef STS_H
+#define STS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sts_status;
+
+enum {
+    STS_OK = 0,
+    STS_ERR_INVALID_ARG = 1,   /* a size, pointer, index array or option is invalid   */
+    STS_ERR_ALLOC = 2,         /* device or host allocation failed                      */
+    STS_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed          */
+    STS_ERR_SINGULAR = 4,      /* zero pivot in S_ii or singular capacitance C_k        */
+    STS_ERR_NOT_CONVERGED = 5, /* GMRES hit max_iters; the returned x is still valid    */
+    STS_ERR_NUMERIC = 6,       /* NaN or Inf met in a residual or Krylov quantity       */
+    STS_ERR_TIMEOUT = 7,       /* reserved for bounded device-side waits                */
+    STS_ERR_NOT_SETUP = 8      /* block-Jacobi used before sts_jac_bjacobi_setup        */
+};
+
+enum { STS_F64 = 0, STS_MIXED = 2 };                       /* sts_jac_desc.dtype        */
+enum { STS_LAYOUT_CELL_MAJOR = 0, STS_LAYOUT_COMPONENT_MAJOR = 1 };
+enum { STS_REP_FACTORED = 0, STS_REP_DENSE_BSR = 1 };      /* sts_jac_desc.representation */
+enum { STS_PRECOND_BJ = 0, STS_PRECOND_NONE = 1 };         /* sts_gmres_opts.precond     */
+
+typedef struct sts_jac_s *sts_jac_t;
+
+/*
+ * Problem statement of one Jacobian (Section 3.4: one block per cell and per
+ * interior face; Section 5.1: BSR index arrays fixed by the mesh adjacency;
+ * Section 6, Eq. R1_Block_Jacobian: A_k = A_k^0 + U_k V_k^T).
+ *
+ *   n_cells, block_size    number of cells and unknowns per cell (b)
+ *   n_levels               quantum levels N (informational; b = N + 3 in the paper's model)
+ *   dtype                  STS_F64: FP64 operators only.
+ *                          STS_MIXED: also keep FP32 copies of the operators for the
+ *                          mixed-precision solver and the *_f32 calls (+50% memory).
+ *   vec_layout             layout of every vector argument (see above)
+ *   representation         STS_REP_FACTORED: the paper's S + rank-one storage.
+ *                          STS_REP_DENSE_BSR: the standard dense-block BSR storage of
+ *                          Section 3.4 (blocks assembled once, b*b values each), kept
+ *                          as the baseline the factored storage is measured against.
+ *   block_indptr[n_cells+1], block_indices[nnzb]   HOST int32.  Block CSR of the mesh
+ *                          adjacency including the diagonal; each row sorted
+ *                          ascending, no duplicates, every row holds its diagonal.
+ *   d_indptr[b+1], d_indices[nnz_d]   HOST int32.  CSR pattern of S_ii, shared by all
+ *                          diagonal blocks; rows sorted, every diagonal entry present.
+ *   o_indptr[b+1], o_indices[nnz_o]   HOST int32.  CSR pattern of S_ij (i != j), shared
+ *                          by all off-diagonal blocks (may be empty).
+ *   r_diag, r_off          rank-one pairs per diagonal / off-diagonal block (>= 0).
+ *                          The BR1-BSR pair_indptr of Section 5.1 follows from them:
+ *                          pairs are numbered in block order.
+ *   S, U, V                FP64 values.  S: block order, nnz_d values per diagonal
+ *                          block and nnz_o per off-diagonal block, each in pattern
+ *                          order.  U (column_data) and V (row_data): [n_pairs][b].
+ *                          Device pointers, or host pointers if values_on_host = 1.
+ *   values_on_host         0: S/U/V are device pointers; 1: host pointers
+ *   enable_transpose       1: also build the transposed operators (needed by
+ *                          trans = 1 calls, the adjoint solve and sts_jac_grad)
+ *   stream                 cudaStream_t to issue all work on (NULL = legacy default)
+ */
+typedef struct {
+    int n_cells;
+    int block_size;
+    int n_levels;
+    int dtype;
+    int vec_layout;
+    int representation;
+    const int *block_indptr;
+    const int *block_indices;
+    const int *d_indptr;
+    const int *d_indices;
+    const int *o_indptr;
+    const int *o_indices;
+    int r_diag;
+    int r_off;
+    const double *S;
+    const double *U;
+    const double *V;
+    int values_on_host;
+    int enable_transpose;
+    void *stream;
+} sts_jac_desc;
+
+/* Options of sts_gmres_solve.  Zero-initialised fields take the defaults shown. */
+typedef struct {
+    int restart;          /* Krylov dimension m per cycle (default 30)                        */
+    int max_iters;        /* total Arnoldi steps over all cycles (default 1000)               */
+    double rtol;          /* stop when ||b - J x|| / ||b|| <= rtol, true FP64 residual (1e-10) */
+    int precond;          /* STS_PRECOND_BJ (default, 0) or STS_PRECOND_NONE                  */
+    int flexible;         /* 1: FGMRES (stores the preconditioned vectors Z)                  */
+    int trans;            /* 1: solve J^T x = b with the transposed operators                 */
+    int mixed;            /* 1: FP32 matvec + FP32 block-Jacobi inside FP64 FGMRES            */
+    double inner_rtol;    /* mixed mode: relative reduction per cycle (default 1e-6)          */
+    int vectors_on_host;  /* 1: b and x are host pointers (copied in and out inside the call) */
+    double *history;      /* optional host array [max_iters]: rotated residual / ||b|| per step */
+} sts_gmres_opts;
+
+/* Result of sts_gmres_solve. */
+typedef struct {
+    int iterations;       /* Arnoldi steps taken                                   */
+    int restarts;         /* cycles completed                                      */
+    int converged;        /* 1 if the true relative residual reached rtol          */
+    double true_rel_residual;  /* ||b - J x|| / ||b||, recomputed in FP64 at the end */
+} sts_gmres_info;
+
+/* Message of the last failed call on this thread ("" if none).  Never NULL. */
+const char *sts_last_error(void);
+
+/* Library version string. */
+const char *sts_version(void);
+
+/*
+ * Create a Jacobian handle from a problem statement (see sts_jac_desc).
+ * Validates every index array (sorted, in range, diagonal present, sizes),
+ * builds the kernels' internal layouts on the host and copies and repacks the
+ * values on the device.  Synchronous.  *out receives the handle (NULL on error).
+ * Errors: STS_ERR_INVALID_ARG, STS_ERR_ALLOC, STS_ERR_CUDA.
+ */
+sts_status sts_jac_create(const sts_jac_desc *desc, sts_jac_t *out);
+
+/*
+ * Replace the values S, U, V (same layouts and residency flag as at creation),
+ * e.g. after a Newton update.  Invalidates the block-Jacobi setup.  Asynchronous.
+ */
+sts_status sts_jac_update_values(sts_jac_t h, const double *S, const double *U,
+                                 const double *V, int values_on_host);
+
+/*
+ * y = J x (trans = 0) or y = J^T x (trans = 1), FP64, device vectors in the
+ * handle's layout (Section 5.2: c_p = v_p . x_col(p) for every pair, then
+ * y_i = sum_j S_ij x_j + sum_{p in row i} c_p u_p).  x and y must not overlap.
+ * trans = 1 needs enable_transpose.  Asynchronous.
+ */
+sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans);
+
+/* FP32 operator, FP32 device vectors (needs dtype STS_MIXED).  Asynchronous. */
+sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans);
+
+/*
+ * Block-Jacobi setup (Section 6).  Factored representation: per cell a static-
+ * pivot sparse LU of S_ii on the symbolic schedule of the shared pattern,
+ * W_k = S_ii^-1 U_k, C_k = I + V_k^T W_k (FP64) and C_k^-1.  Dense-BSR
+ * representation: per-cell dense LU with partial pivoting.  Synchronous.
+ * Errors: STS_ERR_SINGULAR when a pivot fails |p| > 1e-14 * max|row of S_ii|, or
+ * C_k is singular; the message names the first failing cell.
+ */
+sts_status sts_jac_bjacobi_setup(sts_jac_t h);
+
+/*
+ * z = M x with M = blockdiag(J)^-1 (trans = 0) or M^T x (trans = 1):
+ * x0 = S_ii^-1 x_i, t = V^T x0, z_i = x0 - W C^-1 t (Section 6 SMW-1..3, with the
+ * minus sign the Woodbury identity requires).  FP64 device vectors; x and z
+ * must not overlap.  Errors: STS_ERR_NOT_SETUP.  Asynchronous.
+ */
+sts_status sts_jac_bjacobi_apply(sts_jac_t h, const double *x, double *z, int trans);
+
+/* FP32 apply (LU values, W and V rounded to FP32; the r x r solve stays FP64). */
+sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int trans);
+
+/*
+ * Solve J x = b (or J^T x = b) by restarted right-preconditioned GMRES(m)
+ * (Section 6, Eq. right_precond_system; Saad & Schultz), classical Gram-Schmidt
+ * with a second pass, Givens rotations on the host in FP64.  x holds the
+ * initial guess on entry and the solution on exit (pass zeros for x0 = 0).
+ * Mixed mode: FP32 matvec and block-Jacobi, FP64 Krylov basis, Arnoldi,
+ * residual refresh and capacitance solves, flexible GMRES.  Convergence is
+ * declared on the FP64 true residual only.  Synchronous; info may be NULL.
+ * Errors: STS_ERR_NOT_CONVERGED (x valid), STS_ERR_NUMERIC, STS_ERR_NOT_SETUP.
+ */
+sts_status sts_gmres_solve(sts_jac_t h, const double *b, double *x, const sts_gmres_opts *opts,
+                           sts_gmres_info *info);
+
+/*
+ * Adjoint outer products of x = J^-1 b for the adjoint lambda = J^-T g
+ * (derivative of the implicit solve): gS = -lambda_i x_j^T restricted to the
+ * stored pattern of every block, gU[p] = -(v_p . x_j) lambda_i,
+ * gV[p] = -(u_p . lambda_i) x_j.  lambda, x: device vectors in the handle's
+ * layout; gS, gU, gV: device arrays in the public S / U / V layouts.
+ * Needs the factored representation with enable_transpose.  Asynchronous.
+ */
+sts_status sts_jac_grad(sts_jac_t h, const double *lambda, const double *x, double *gS,
+                        double *gU, double *gV);
+
+/*
+ * Device bytes held by the handle (values, internal layouts, setup data,
+ * workspaces).  Synchronous; never fails for a valid handle.
+ */
+sts_status sts_jac_memory(sts_jac_t h, size_t *bytes);
+
+/*
+ * Number of CUDA kernels this library has launched since it was loaded, over
+ * all handles and threads (instrumentation for benchmarks).  Never fails for a
+ * non-NULL count.
+ */
+sts_status sts_launch_count(unsigned long long *count);
+
+/* Destroy a handle and free its device memory.  NULL is accepted. */
+sts_status sts_jac_destroy(sts_jac_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STS_H */

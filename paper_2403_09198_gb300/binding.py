@@ -1,0 +1,277 @@
+"""ctypes binding of ``libsts.so`` (C ABI in ``include/sts.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  There is no
+CPU fallback: if the library is not built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsts.so")
+
+STS_OK = 0
+STATUS_NAMES = {0: "STS_OK", 1: "STS_ERR_INVALID_ARG", 2: "STS_ERR_ALLOC", 3: "STS_ERR_CUDA",
+                4: "STS_ERR_SINGULAR", 5: "STS_ERR_NOT_CONVERGED", 6: "STS_ERR_NUMERIC",
+                7: "STS_ERR_TIMEOUT", 8: "STS_ERR_NOT_SETUP"}
+STS_F64, STS_MIXED = 0, 2
+STS_LAYOUT_CELL_MAJOR, STS_LAYOUT_COMPONENT_MAJOR = 0, 1
+STS_REP_FACTORED, STS_REP_DENSE_BSR = 0, 1
+STS_PRECOND_BJ, STS_PRECOND_NONE = 0, 1
+
+# Every entry point declared in include/sts.h.
+ABI_FUNCTIONS = ["sts_last_error", "sts_version", "sts_jac_create", "sts_jac_update_values",
+                 "sts_jac_matvec", "sts_jac_matvec_f32", "sts_jac_bjacobi_setup",
+                 "sts_jac_bjacobi_apply", "sts_jac_bjacobi_apply_f32", "sts_gmres_solve",
+                 "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_jac_destroy"]
+
+
+class sts_jac_desc(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("block_size", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("dtype", ctypes.c_int), ("vec_layout", ctypes.c_int),
+                ("representation", ctypes.c_int),
+                ("block_indptr", ctypes.c_void_p), ("block_indices", ctypes.c_void_p),
+                ("d_indptr", ctypes.c_void_p), ("d_indices", ctypes.c_void_p),
+                ("o_indptr", ctypes.c_void_p), ("o_indices", ctypes.c_void_p),
+                ("r_diag", ctypes.c_int), ("r_off", ctypes.c_int),
+                ("S", ctypes.c_void_p), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("values_on_host", ctypes.c_int), ("enable_transpose", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class sts_gmres_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("precond", ctypes.c_int), ("flexible", ctypes.c_int), ("trans", ctypes.c_int),
+                ("mixed", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("vectors_on_host", ctypes.c_int), ("history", ctypes.c_void_p)]
+
+
+class sts_gmres_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double)]
+
+
+class StsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"{path} is missing: build it with paper_2403_09198_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            P, I = ctypes.c_void_p, ctypes.c_int
+            lib.sts_last_error.restype = ctypes.c_char_p
+            lib.sts_last_error.argtypes = []
+            lib.sts_version.restype = ctypes.c_char_p
+            lib.sts_version.argtypes = []
+            sig = {
+                "sts_jac_create": [ctypes.POINTER(sts_jac_desc), ctypes.POINTER(P)],
+                "sts_jac_update_values": [P, P, P, P, I],
+                "sts_jac_matvec": [P, P, P, I],
+                "sts_jac_matvec_f32": [P, P, P, I],
+                "sts_jac_bjacobi_setup": [P],
+                "sts_jac_bjacobi_apply": [P, P, P, I],
+                "sts_jac_bjacobi_apply_f32": [P, P, P, I],
+                "sts_gmres_solve": [P, P, P, ctypes.POINTER(sts_gmres_opts),
+                                    ctypes.POINTER(sts_gmres_info)],
+                "sts_jac_grad": [P, P, P, P, P, P],
+                "sts_jac_memory": [P, ctypes.POINTER(ctypes.c_size_t)],
+                "sts_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
+                "sts_jac_destroy": [P],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = I
+            _lib = lib
+    return _lib
+
+
+def check(status: int, allow=()) -> int:
+    if status != STS_OK and status not in allow:
+        raise StsError(status, load().sts_last_error().decode(errors="replace"))
+    return status
+
+
+def launch_count() -> int:
+    """Kernels launched by the CUDA library since it was loaded."""
+    n = ctypes.c_ulonglong()
+    check(load().sts_launch_count(ctypes.byref(n)))
+    return int(n.value)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+@dataclass
+class GmresInfo:
+    iterations: int
+    restarts: int
+    converged: bool
+    true_rel_residual: float
+    history: np.ndarray | None = None
+
+
+class StsJacobian:
+    """Owner of one ``sts_jac_t`` handle.
+
+    ``w`` is any object exposing the public layout arrays (``block_indptr``,
+    ``block_indices``, ``d_indptr``, ``d_indices``, ``o_indptr``, ``o_indices``,
+    ``r_diag``, ``r_off``, ``b``); ``S``, ``U``, ``V`` are FP64 torch CUDA tensors
+    or numpy arrays (host), in the public layout.
+    """
+
+    def __init__(self, w, S, U, V, *, mixed: bool = False, layout: str = "cell",
+                 dense: bool = False, transpose: bool = False, stream=None, n_levels: int = 0):
+        import torch
+        self.lib = load()
+        self.b = int(w.b)
+        self.n_cells = int(np.asarray(w.block_indptr).shape[0] - 1)
+        self.layout = layout
+        self._idx = [np.ascontiguousarray(a, dtype=np.int32) for a in
+                     (w.block_indptr, w.block_indices, w.d_indptr, w.d_indices, w.o_indptr,
+                      w.o_indices)]
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        on_host = isinstance(S, np.ndarray)
+        if on_host:
+            S, U, V = (np.ascontiguousarray(a, dtype=np.float64) for a in (S, U, V))
+        else:
+            for a in (S, U, V):
+                if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+                    raise ValueError("S, U, V must be contiguous float64 CUDA tensors or numpy arrays")
+        d = sts_jac_desc()
+        d.n_cells = self.n_cells
+        d.block_size = self.b
+        d.n_levels = int(n_levels or getattr(w, "N", 0))
+        d.dtype = STS_MIXED if mixed else STS_F64
+        d.vec_layout = STS_LAYOUT_CELL_MAJOR if layout == "cell" else STS_LAYOUT_COMPONENT_MAJOR
+        d.representation = STS_REP_DENSE_BSR if dense else STS_REP_FACTORED
+        (d.block_indptr, d.block_indices, d.d_indptr, d.d_indices, d.o_indptr,
+         d.o_indices) = [a.ctypes.data for a in self._idx]
+        d.r_diag = int(w.r_diag)
+        d.r_off = int(w.r_off)
+        d.S, d.U, d.V = _ptr(S), _ptr(U), _ptr(V)
+        d.values_on_host = 1 if on_host else 0
+        d.enable_transpose = 1 if transpose else 0
+        d.stream = self.stream.cuda_stream
+        h = ctypes.c_void_p()
+        check(self.lib.sts_jac_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self.mixed = mixed
+        self.n = self.n_cells * self.b
+        # sizes of the public value arrays (index bookkeeping only)
+        bptr, bidx = self._idx[0], self._idx[1]
+        rows = np.repeat(np.arange(self.n_cells), np.diff(bptr))
+        n_diag = int(np.sum(rows == bidx))
+        n_off = int(bidx.shape[0]) - n_diag
+        self.nnz_S = n_diag * int(self._idx[2][-1]) + n_off * int(self._idx[4][-1])
+        self.n_pairs = n_diag * int(w.r_diag) + n_off * int(w.r_off)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sts_jac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls
+    def update_values(self, S, U, V):
+        on_host = isinstance(S, np.ndarray)
+        if on_host:
+            S, U, V = (np.ascontiguousarray(a, dtype=np.float64) for a in (S, U, V))
+        check(self.lib.sts_jac_update_values(self.h, _ptr(S), _ptr(U), _ptr(V), int(on_host)))
+        if on_host:
+            self.stream.synchronize()   # host arrays must outlive the copies
+
+    def matvec(self, x, out=None, trans: bool = False):
+        import torch
+        y = torch.empty_like(x) if out is None else out
+        if x.dtype == torch.float32:
+            check(self.lib.sts_jac_matvec_f32(self.h, _ptr(x), _ptr(y), int(trans)))
+        else:
+            check(self.lib.sts_jac_matvec(self.h, _ptr(x), _ptr(y), int(trans)))
+        return y
+
+    def bjacobi_setup(self):
+        check(self.lib.sts_jac_bjacobi_setup(self.h))
+
+    def bjacobi_apply(self, x, out=None, trans: bool = False):
+        import torch
+        z = torch.empty_like(x) if out is None else out
+        if x.dtype == torch.float32:
+            check(self.lib.sts_jac_bjacobi_apply_f32(self.h, _ptr(x), _ptr(z), int(trans)))
+        else:
+            check(self.lib.sts_jac_bjacobi_apply(self.h, _ptr(x), _ptr(z), int(trans)))
+        return z
+
+    def gmres(self, b, x0=None, *, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1000,
+              precond: str = "bj", trans: bool = False, mixed: bool = False,
+              inner_rtol: float = 0.0, history: bool = False, raise_on_fail: bool = True):
+        """Solve J x = b (J^T x = b).  ``b``: CUDA tensor or numpy array (host)."""
+        import torch
+        on_host = isinstance(b, np.ndarray)
+        if on_host:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        else:
+            x = torch.zeros_like(b) if x0 is None else x0.clone()
+        o = sts_gmres_opts()
+        o.restart, o.max_iters, o.rtol = restart, max_iters, rtol
+        o.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
+        o.trans, o.mixed, o.inner_rtol = int(trans), int(mixed), inner_rtol
+        o.vectors_on_host = int(on_host)
+        hist = np.zeros(max_iters) if history else None
+        o.history = hist.ctypes.data if history else None
+        info = sts_gmres_info()
+        st = self.lib.sts_gmres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        if raise_on_fail:
+            check(st)
+        gi = GmresInfo(info.iterations, info.restarts, bool(info.converged), info.true_rel_residual,
+                       hist[:info.iterations].copy() if history else None)
+        return x, gi
+
+    def grad(self, lam, x):
+        """Adjoint outer products (gS, gU, gV) in the public S / U / V layouts."""
+        import torch
+        gS = torch.empty(self.nnz_S, dtype=torch.float64, device=lam.device)
+        gU = torch.empty((self.n_pairs, self.b), dtype=torch.float64, device=lam.device)
+        gV = torch.empty_like(gU)
+        check(self.lib.sts_jac_grad(self.h, _ptr(lam), _ptr(x), _ptr(gS), _ptr(gU), _ptr(gV)))
+        return gS, gU, gV
+
+    def memory_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(self.lib.sts_jac_memory(self.h, ctypes.byref(n)))
+        return int(n.value)

@@ -1,0 +1,405 @@
+// kernels_krylov.cu -- restarted right-preconditioned GMRES(m) on the device.
+//
+// Section 6 (Eq. right_precond_system): solve (A M) y = b, x = M y.  Each
+// cycle starts from the true FP64 residual r = b - A x, builds the Krylov basis
+// by classical Gram-Schmidt with a second pass (CGS2: two fused multi-dot +
+// update sweeps per step, same result as modified Gram-Schmidt in exact
+// arithmetic), reduces the Hessenberg matrix with Givens rotations on the host
+// in FP64 and updates x += Z y with Z = [M v_0, ..., M v_{k-1}] (for a fixed M
+// this equals x += M (V y)).  Convergence is declared on the recomputed true
+// residual only.  Mixed mode (flexible GMRES): z_j = M32(v_j) and w = A32 z_j in
+// FP32; the basis, the orthogonalisation, x and the residual refresh stay FP64.
+//
+// All reductions are deterministic: a fixed grid writes per-block partial sums
+// in a fixed order and one block adds them in a fixed order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "sts_internal.h"
+
+namespace sts {
+namespace {
+
+constexpr int kRedBlocks = 304;     // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+constexpr int kDotChunk = 16;       // vectors per multi-dot sweep
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+// partial[blk * ld + i0 + i] = sum over this block's elements of V_{i0+i} . w,
+// for i < cnt (cnt <= kDotChunk).  With self = 1 the last slot holds w . w.
+__global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long n, int i0, int cnt,
+                                                      const double *w, double *partial, int ld,
+                                                      int self) {
+    __shared__ double sh[kRedThreads / 32];
+    double acc[kDotChunk + 1];
+#pragma unroll
+    for (int i = 0; i <= kDotChunk; ++i) acc[i] = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double we = w[e];
+#pragma unroll
+        for (int i = 0; i < kDotChunk; ++i)
+            if (i < cnt) acc[i] = fma(V[(size_t)(i0 + i) * n + e], we, acc[i]);
+        if (self) acc[kDotChunk] = fma(we, we, acc[kDotChunk]);
+    }
+    for (int i = 0; i < cnt; ++i) {
+        const double s = block_sum(acc[i], sh);
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + i] = s;
+    }
+    if (self) {
+        const double s = block_sum(acc[kDotChunk], sh);
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + cnt] = s;
+    }
+}
+
+// out[i] = sum_b partial[b * ld + i], fixed order.
+__global__ void k_reduce(const double *partial, int nblk, int ld, int cnt, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * ld + i];
+    out[i] = s;
+}
+
+// w -= sum_{i<k} h_i V_i; with norm = 1 also partial[blk] = sum w^2 after the update.
+__global__ void __launch_bounds__(kRedThreads) k_update(double *w, const double *V, long long n,
+                                                        const double *hcoef, int k, double *partial,
+                                                        int norm) {
+    __shared__ double sh[kRedThreads / 32];
+    __shared__ double hs[64];
+    double acc = 0.0;
+    for (int i0 = 0; i0 < k; i0 += 64) {
+        const int cnt = min(64, k - i0);
+        __syncthreads();
+        if (threadIdx.x < cnt) hs[threadIdx.x] = hcoef[i0 + threadIdx.x];
+        __syncthreads();
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (long long)gridDim.x * blockDim.x) {
+            double v = w[e];
+            for (int i = 0; i < cnt; ++i) v = fma(-hs[i], V[(size_t)(i0 + i) * n + e], v);
+            w[e] = v;
+        }
+    }
+    if (norm) {
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (long long)gridDim.x * blockDim.x)
+            acc = fma(w[e], w[e], acc);
+        const double s = block_sum(acc, sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const double *v, long long n, double *partial) {
+    __shared__ double sh[kRedThreads / 32];
+    double acc = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        acc = fma(v[e], v[e], acc);
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_sub(double *r, const double *b, const double *y, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        r[e] = b[e] - y[e];
+}
+
+__global__ void k_scale(double *out, const double *in, double s, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = in[e] * s;
+}
+
+template <typename T>
+__global__ void k_axpy_multi(double *x, const T *Z, long long n, const double *y, int k) {
+    __shared__ double ys[64];
+    for (int i0 = 0; i0 < k; i0 += 64) {
+        const int cnt = min(64, k - i0);
+        __syncthreads();
+        if (threadIdx.x < cnt) ys[threadIdx.x] = y[i0 + threadIdx.x];
+        __syncthreads();
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+             e += (long long)gridDim.x * blockDim.x) {
+            double v = x[e];
+            for (int i = 0; i < cnt; ++i) v = fma(ys[i], (double)Z[(size_t)(i0 + i) * n + e], v);
+            x[e] = v;
+        }
+    }
+}
+
+template <typename To, typename Ti>
+__global__ void k_convert(To *out, const Ti *in, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = (To)in[e];
+}
+
+inline int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 32) g = 152LL * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Operators shared with the public entry points.
+sts_status opA64(sts_jac_s *h, int dir, const double *x, double *y) {
+    if (h->rep == STS_REP_DENSE_BSR) return dense_matvec(h, x, y);
+    return mv_apply64(h, dir, x, y, h->c64);
+}
+sts_status opM64(sts_jac_s *h, int dir, const double *x, double *z) {
+    if (h->rep == STS_REP_DENSE_BSR) return dense_apply(h, x, z);
+    return smw_apply64(h, dir, x, z);
+}
+
+struct Red {
+    sts_jac_s *h;
+    long long n;
+    // device: partial [kRedBlocks][ld], reduced values land in h->kry.red
+    sts_status dots(const double *V, int k, const double *w, int self, double *out) {
+        Krylov &K = h->kry;
+        const int ld = K.m + 2;
+        for (int i0 = 0; i0 < k; i0 += kDotChunk) {
+            const int cnt = std::min(kDotChunk, k - i0);
+            const int sf = self && (i0 + cnt == k);
+            k_mdot<<<kRedBlocks, kRedThreads, 0, h->stream>>>(V, n, i0, cnt, w, K.partial, ld, sf);
+            STS_LAUNCHED();
+        }
+        k_reduce<<<(k + (self ? 1 : 0) + 63) / 64, 64, 0, h->stream>>>(K.partial, kRedBlocks, ld, k + (self ? 1 : 0), out);
+        STS_LAUNCHED();
+        return STS_OK;
+    }
+    sts_status update(double *w, const double *V, int k, const double *hcoef, int norm, double *out) {
+        Krylov &K = h->kry;
+        k_update<<<kRedBlocks, kRedThreads, 0, h->stream>>>(w, V, n, hcoef, k, K.partial, norm);
+        STS_LAUNCHED();
+        if (norm) {
+            k_reduce<<<1, 64, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
+            STS_LAUNCHED();
+        }
+        return STS_OK;
+    }
+    sts_status norm2(const double *v, double *out) {
+        Krylov &K = h->kry;
+        k_norm2<<<kRedBlocks, kRedThreads, 0, h->stream>>>(v, n, K.partial);
+        STS_LAUNCHED();
+        k_reduce<<<1, 64, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
+        STS_LAUNCHED();
+        return STS_OK;
+    }
+};
+
+sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
+    Krylov &K = h->kry;
+    const size_t n = (size_t)h->b * h->ncp;
+    if (K.m < m) {
+        // the old buffers stay owned by the handle (freed at destroy); only grow
+        STS_TRY(dalloc(h, &K.V, (size_t)(m + 1) * n));
+        STS_TRY(dalloc(h, &K.Z, (size_t)m * n));
+        K.Z32 = nullptr;
+        STS_TRY(dalloc(h, &K.partial, (size_t)kRedBlocks * (m + 2)));
+        STS_TRY(dalloc(h, &K.red, (size_t)3 * (m + 2)));
+        if (!K.w) {
+            STS_TRY(dalloc(h, &K.w, n));
+            STS_TRY(dalloc(h, &K.r, n));
+            STS_TRY(dalloc(h, &K.xb, n));
+            STS_TRY(dalloc(h, &K.bb, n));
+            STS_TRY(dalloc(h, &K.tmp, n));
+        }
+        if (K.h_pinned) cudaFreeHost(K.h_pinned);
+        K.h_pinned = nullptr;
+        STS_CK(cudaMallocHost(&K.h_pinned, sizeof(double) * 3 * (m + 2)));
+        K.m = m;
+    }
+    if (mixed && !K.Z32) {
+        STS_TRY(dalloc(h, &K.Z32, (size_t)K.m * n));
+        if (!K.t32a) {
+            STS_TRY(dalloc(h, &K.t32a, n));
+            STS_TRY(dalloc(h, &K.t32b, n));
+        }
+    }
+    return STS_OK;
+}
+
+}  // namespace
+
+sts_status op_matvec64(sts_jac_s *h, int dir, const double *x, double *y) { return opA64(h, dir, x, y); }
+sts_status op_apply64(sts_jac_s *h, int dir, const double *x, double *z) { return opM64(h, dir, x, z); }
+
+sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmres_opts *o,
+                 sts_gmres_info *info) {
+    sts_gmres_opts d{};
+    if (o) d = *o;
+    const int m = d.restart > 0 ? d.restart : 30;
+    const int max_iters = d.max_iters > 0 ? d.max_iters : 1000;
+    const double rtol = d.rtol > 0 ? d.rtol : 1e-10;
+    const double inner = d.inner_rtol > 0 ? d.inner_rtol : 1e-6;
+    const bool pre = d.precond != STS_PRECOND_NONE;
+    const int dir = d.trans ? 1 : 0;
+    const bool mixed = d.mixed != 0;
+    if (d.precond != STS_PRECOND_BJ && d.precond != STS_PRECOND_NONE)
+        return set_error(STS_ERR_INVALID_ARG, "gmres: unknown precond %d", d.precond);
+    if (m > 512) return set_error(STS_ERR_INVALID_ARG, "gmres: restart %d exceeds 512", m);
+    if (dir == 1 && (!h->has_T || h->rep != STS_REP_FACTORED))
+        return set_error(STS_ERR_INVALID_ARG, "gmres: trans = 1 needs a factored handle created with enable_transpose");
+    if (mixed && (h->dtype != STS_MIXED || h->rep != STS_REP_FACTORED))
+        return set_error(STS_ERR_INVALID_ARG, "gmres: mixed = 1 needs a factored handle created with dtype STS_MIXED");
+    if (pre) {
+        const bool ready = h->rep == STS_REP_FACTORED ? h->smw.ready : h->dense.ready;
+        if (!ready) return set_error(STS_ERR_NOT_SETUP, "gmres: block-Jacobi preconditioner used before sts_jac_bjacobi_setup");
+    }
+    STS_TRY(ensure_workspace(h, m, mixed));
+    Krylov &K = h->kry;
+    const long long n = (long long)h->b * h->ncp;
+    Red R{h, n};
+    const int nb = grid_for(n, 256);
+    const size_t vbytes = (size_t)h->nc * h->b * sizeof(double);
+    // inputs into the internal layout
+    const double *b_src = b_pub;
+    const double *x_src = x_pub;
+    if (d.vectors_on_host) {
+        STS_CK(cudaMemcpyAsync(h->vin, b_pub, vbytes, cudaMemcpyHostToDevice, h->stream));
+        STS_TRY(to_internal64(h, h->vin, K.bb));
+        STS_CK(cudaMemcpyAsync(h->vin, x_pub, vbytes, cudaMemcpyHostToDevice, h->stream));
+        STS_TRY(to_internal64(h, h->vin, K.xb));
+    } else {
+        STS_TRY(to_internal64(h, b_src, K.bb));
+        STS_TRY(to_internal64(h, x_src, K.xb));
+    }
+    double *hp = K.h_pinned;
+    STS_TRY(R.norm2(K.bb, K.red));
+    STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    STS_CK(cudaStreamSynchronize(h->stream));
+    const double bnorm = std::sqrt(hp[0]);
+    if (!std::isfinite(bnorm)) return set_error(STS_ERR_NUMERIC, "gmres: right-hand side has NaN or Inf");
+    sts_gmres_info inf{0, 0, 1, 0.0};
+    sts_status status = STS_OK;
+    if (bnorm == 0.0) {
+        STS_CK(cudaMemsetAsync(K.xb, 0, n * sizeof(double), h->stream));
+    } else {
+        std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+        int its = 0;
+        for (;;) {
+            // true residual r = b - A x
+            STS_TRY(opA64(h, dir, K.xb, K.w));
+            k_sub<<<nb, 256, 0, h->stream>>>(K.r, K.bb, K.w, n);
+            STS_LAUNCHED();
+            STS_TRY(R.norm2(K.r, K.red));
+            STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            STS_CK(cudaStreamSynchronize(h->stream));
+            const double beta = std::sqrt(hp[0]);
+            if (!std::isfinite(beta)) {
+                status = set_error(STS_ERR_NUMERIC, "gmres: residual norm is NaN or Inf");
+                break;
+            }
+            inf.true_rel_residual = beta / bnorm;
+            if (beta / bnorm <= rtol) { inf.converged = 1; break; }
+            if (its >= max_iters) { inf.converged = 0; break; }
+            const double stop_abs = mixed ? std::max(rtol * bnorm, inner * beta) : rtol * bnorm;
+            k_scale<<<nb, 256, 0, h->stream>>>(K.V, K.r, 1.0 / beta, n);
+            STS_LAUNCHED();
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int k = 0;
+            for (int j = 0; j < m; ++j) {
+                double *vj = K.V + (size_t)j * n;
+                // z_j = M v_j, w = A z_j
+                if (!mixed) {
+                    double *zj = K.Z + (size_t)j * n;
+                    if (pre) STS_TRY(opM64(h, dir, vj, zj));
+                    else STS_CK(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+                    STS_TRY(opA64(h, dir, zj, K.w));
+                } else {
+                    float *zj = K.Z32 + (size_t)j * n;
+                    k_convert<float, double><<<nb, 256, 0, h->stream>>>(pre ? K.t32a : zj, vj, n);
+                    STS_LAUNCHED();
+                    if (pre) STS_TRY(smw_apply32(h, dir, K.t32a, zj));
+                    STS_TRY(mv_apply32(h, dir, zj, K.t32b, h->c32));
+                    k_convert<double, float><<<nb, 256, 0, h->stream>>>(K.w, K.t32b, n);
+                    STS_LAUNCHED();
+                }
+                // CGS2: h1 = V^T w (+ w.w), w -= V h1; h2 = V^T w, w -= V h2, ||w||^2
+                double *h1 = K.red, *h2 = K.red + (m + 2), *nr = K.red + 2 * (m + 2);
+                STS_TRY(R.dots(K.V, j + 1, K.w, 1, h1));
+                STS_TRY(R.update(K.w, K.V, j + 1, h1, 0, nullptr));
+                STS_TRY(R.dots(K.V, j + 1, K.w, 0, h2));
+                STS_TRY(R.update(K.w, K.V, j + 1, h2, 1, nr));
+                STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaStreamSynchronize(h->stream));
+                const double *H1 = hp, *H2 = hp + (m + 2);
+                const double w0 = std::sqrt(H1[j + 1]);
+                double hn = std::sqrt(hp[2 * (m + 2)]);
+                bool bad = !std::isfinite(w0) || !std::isfinite(hn);
+                for (int i = 0; i <= j; ++i) {
+                    H[(size_t)i * m + j] = H1[i] + H2[i];
+                    bad = bad || !std::isfinite(H[(size_t)i * m + j]);
+                }
+                if (bad) { status = set_error(STS_ERR_NUMERIC, "gmres: NaN or Inf in the Arnoldi process"); break; }
+                H[(size_t)(j + 1) * m + j] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                    H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                    H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+                }
+                const double hjj = H[(size_t)j * m + j];
+                const double den = std::hypot(hjj, hn);
+                cs[j] = hjj / den;
+                sn[j] = hn / den;
+                H[(size_t)j * m + j] = den;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                ++its;
+                k = j + 1;
+                if (d.history && its <= max_iters) d.history[its - 1] = std::fabs(g[j + 1]) / bnorm;
+                const bool happy = hn <= 1e-14 * w0;
+                if (happy || std::fabs(g[j + 1]) <= stop_abs || its >= max_iters) break;
+                k_scale<<<nb, 256, 0, h->stream>>>(K.V + (size_t)(j + 1) * n, K.w, 1.0 / hn, n);
+                STS_LAUNCHED();
+            }
+            if (status != STS_OK) break;
+            for (int i = k - 1; i >= 0; --i) {
+                double s = g[i];
+                for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+                y[i] = s / H[(size_t)i * m + i];
+            }
+            std::copy(y.begin(), y.begin() + k, hp);
+            STS_CK(cudaMemcpyAsync(K.red, hp, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+            if (!mixed) k_axpy_multi<double><<<nb, 256, 0, h->stream>>>(K.xb, K.Z, n, K.red, k);
+            else k_axpy_multi<float><<<nb, 256, 0, h->stream>>>(K.xb, K.Z32, n, K.red, k);
+            STS_LAUNCHED();
+            ++inf.restarts;
+        }
+        inf.iterations = its;
+    }
+    if (status == STS_OK || status == STS_ERR_NOT_CONVERGED) {
+        if (d.vectors_on_host) {
+            STS_TRY(from_internal64(h, K.xb, h->vout));
+            STS_CK(cudaMemcpyAsync(x_pub, h->vout, vbytes, cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            STS_TRY(from_internal64(h, K.xb, x_pub));
+        }
+        STS_CK(cudaStreamSynchronize(h->stream));
+    }
+    if (info) *info = inf;
+    if (status != STS_OK) return status;
+    if (!inf.converged)
+        return set_error(STS_ERR_NOT_CONVERGED, "gmres: %d iterations, true relative residual %.3e > rtol %.3e",
+                         inf.iterations, inf.true_rel_residual, rtol);
+    return STS_OK;
+}
+
+}  // namespace sts

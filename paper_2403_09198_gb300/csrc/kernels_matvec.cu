@@ -1,0 +1,381 @@
+// kernels_matvec.cu -- the factored Jacobian-vector product (Section 5.2).
+//
+//   c_p = v_p . x_col(p)                      for every rank-one pair p   (pass 1)
+//   y_i = sum_j S_ij x_j + sum_{p in row i} c_p u_p                       (pass 2)
+//
+// The paper's CPU listing computes pass 1 for one block row and then
+// accumulates that row; here pass 1 runs for all pairs first (one warp per
+// tile and pair slot) and pass 2 runs one warp per (tile, row group).  In both
+// passes lane = cell, each lane accumulates its own sums serially (one FMA per
+// multiply-add, no cross-lane reduction), and every stream value is read once
+// with a coalesced 32-lane request.  The transposed product J^T x uses the
+// same kernels on the transposed plan (S^T patterns, roles of u and v swapped).
+#include <cuda_runtime.h>
+
+#include "sts_internal.h"
+
+namespace sts {
+namespace {
+
+template <typename T>
+struct MvArgs {
+    const T *main;          // [n_tiles][tile_len][32]
+    const T *dotv;          // [n_tiles][n_pslots][b][32]
+    const T *x;             // [b][ncp]
+    T *y;                   // [b][ncp]
+    T *c;                   // [n_tiles][n_pslots][32]
+    const int *nbr;         // [n_tiles][n_slots][32]
+    const unsigned *slot_mask;
+    const int *grp_rows;
+    const long long *row_off;
+    const int *pslot_slot;
+    const int *pat_ptr;     // [2][b+1]
+    const int *pat_idx;
+    const unsigned *desc;   // [tile_len] program of the main pass
+    long long tile_len;
+    int n_tiles, n_slots, n_pslots, n_groups, b, ncp, nnz_d;
+};
+
+// Chunk of stream positions held in registers; the next chunk is loaded while
+// the current one is consumed, so every warp keeps CH coalesced requests in
+// flight independently of its FMA dependency chain.
+template <typename T> struct Chunk { static constexpr int CH = 8; };
+template <> struct Chunk<float> { static constexpr int CH = 16; };
+
+// Pass 1: one warp per (tile, pair slot); lane = cell; serial dot over q.
+template <typename T>
+__global__ void __launch_bounds__(128) k_pair_dots(MvArgs<T> a) {
+    constexpr int CH = Chunk<T>::CH;
+    const int lane = threadIdx.x & 31;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= (long long)a.n_tiles * a.n_pslots) return;
+    const int t = (int)(wid / a.n_pslots), k = (int)(wid % a.n_pslots);
+    const int s = a.pslot_slot[k];
+    T acc = T(0);
+    if ((a.slot_mask[t] >> s) & 1u) {
+        const int j = a.nbr[((size_t)t * a.n_slots + s) * kTile + lane];
+        const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_pslots + k) * a.b * kTile + lane;
+        const T *__restrict__ xj = a.x + (j < 0 ? 0 : j);
+        const bool on = j >= 0;
+        const int L = a.b;
+        T cur[CH], nxt[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) cur[i] = i < L ? __ldg(dv + (size_t)i * kTile) : T(0);
+        for (int base = 0; base < L; base += CH) {
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int pp = base + CH + i;
+                nxt[i] = pp < L ? __ldg(dv + (size_t)pp * kTile) : T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int q = base + i;
+                if (q < L) {
+                    const T xv = on ? __ldg(xj + (size_t)q * a.ncp) : T(0);
+                    acc = fma(cur[i], xv, acc);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CH; ++i) cur[i] = nxt[i];
+        }
+    }
+    a.c[((size_t)t * a.n_pslots + k) * kTile + lane] = acc;
+}
+
+// Pass 2: one warp per (tile, row group); lane = cell.  The group's stream
+// positions are consumed in order under a flat program (one descriptor per
+// position: column and block slot of an S entry, or the pair slot of a pair
+// term, plus an end-of-row flag); each row is accumulated serially.
+template <typename T>
+__global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
+    constexpr int CH = Chunk<T>::CH;
+    __shared__ int snb[4][kMaxSlots][kTile];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (wid >= (long long)a.n_tiles * a.n_groups) return;
+    const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
+    for (int s = 0; s < a.n_slots; ++s) snb[wib][s][lane] = a.nbr[((size_t)t * a.n_slots + s) * kTile + lane];
+    __syncwarp();
+    const int p0 = a.grp_rows[g], p1 = a.grp_rows[g + 1];
+    const long long q0 = a.row_off[p0];
+    const int L = (int)(a.row_off[p1] - q0);
+    const T *__restrict__ sv = a.main + ((size_t)t * a.tile_len + q0) * kTile + lane;
+    const unsigned *__restrict__ dd = a.desc + q0;
+    const T *__restrict__ xp = a.x;
+    const T *__restrict__ cc = a.c + (size_t)t * a.n_pslots * kTile + lane;
+    T *__restrict__ yp = a.y + (size_t)p0 * a.ncp + (size_t)t * kTile + lane;
+    T cur[CH], nxt[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) cur[i] = i < L ? __ldg(sv + (size_t)i * kTile) : T(0);
+    T acc = T(0);
+    for (int base = 0; base < L; base += CH) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int pp = base + CH + i;
+            nxt[i] = pp < L ? __ldg(sv + (size_t)pp * kTile) : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int pp = base + i;
+            if (pp < L) {
+                const unsigned d = __ldg(dd + pp);
+                T opnd;
+                if (d & kDescPair) {
+                    opnd = __ldg(cc + (size_t)(d & 0xffffu) * kTile);
+                } else {
+                    const int j = snb[wib][(d >> 16) & 0x1fu][lane];
+                    opnd = j >= 0 ? __ldg(xp + (size_t)(d & 0xffffu) * a.ncp + j) : T(0);
+                }
+                acc = fma(cur[i], opnd, acc);
+                if (d & kDescEnd) {
+                    *yp = acc;
+                    yp += a.ncp;
+                    acc = T(0);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) cur[i] = nxt[i];
+    }
+}
+
+// Repack the public values into the main stream of one direction.
+template <typename T>
+__global__ void k_repack_main(T *out, const double *S, const double *AX, const int *blk,
+                              const long long *soff, const int *pbase, const int *pos_kind,
+                              const int *pos_arg, const int *pat_src, const int *pslot_slot,
+                              const int *pslot_local, long long tile_len, int n_tiles, int n_slots,
+                              int b) {
+    const long long total = (long long)n_tiles * tile_len * kTile;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int lane = (int)(i % kTile);
+        const long long r = i / kTile;
+        const long long pos = r % tile_len;
+        const int t = (int)(r / tile_len);
+        const int kind = pos_kind[pos], arg = pos_arg[pos];
+        double v = 0.0;
+        if (kind >= 0) {
+            const int k = blk[((size_t)t * n_slots + kind) * kTile + lane];
+            if (k >= 0) v = S[soff[k] + pat_src[arg]];
+        } else {
+            const int ps = -1 - kind;
+            const int k = blk[((size_t)t * n_slots + pslot_slot[ps]) * kTile + lane];
+            if (k >= 0) v = AX[(size_t)(pbase[k] + pslot_local[ps]) * b + arg];
+        }
+        out[i] = (T)v;
+    }
+}
+
+template <typename T>
+__global__ void k_repack_dots(T *out, const double *DV, const int *blk, const int *pbase,
+                              const int *pslot_slot, const int *pslot_local, int n_tiles,
+                              int n_slots, int n_pslots, int b) {
+    const long long total = (long long)n_tiles * n_pslots * b * kTile;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int lane = (int)(i % kTile);
+        long long r = i / kTile;
+        const int q = (int)(r % b);
+        r /= b;
+        const int ps = (int)(r % n_pslots);
+        const int t = (int)(r / n_pslots);
+        const int k = blk[((size_t)t * n_slots + pslot_slot[ps]) * kTile + lane];
+        double v = 0.0;
+        if (k >= 0) v = DV[(size_t)(pbase[k] + pslot_local[ps]) * b + q];
+        out[i] = (T)v;
+    }
+}
+
+// Public vector -> internal [b][ncp].  Cell-major input is transposed through
+// shared memory in 32 x 32 tiles so that both sides are coalesced.
+template <typename T>
+__global__ void k_cell_to_comp(const T *__restrict__ x, T *__restrict__ xi, int nc, int b, int ncp) {
+    __shared__ T tile[32][33];
+    const int c0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, q = q0 + threadIdx.x;
+        tile[r][threadIdx.x] = (c < nc && q < b) ? x[(size_t)c * b + q] : T(0);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int q = q0 + r, c = c0 + threadIdx.x;
+        if (q < b && c < ncp) xi[(size_t)q * ncp + c] = tile[threadIdx.x][r];
+    }
+}
+
+template <typename T>
+__global__ void k_comp_to_cell(const T *__restrict__ xi, T *__restrict__ x, int nc, int b, int ncp) {
+    __shared__ T tile[32][33];
+    const int c0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int q = q0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (q < b && c < ncp) ? xi[(size_t)q * ncp + c] : T(0);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, q = q0 + threadIdx.x;
+        if (c < nc && q < b) x[(size_t)c * b + q] = tile[threadIdx.x][r];
+    }
+}
+
+template <typename T>
+__global__ void k_comp_pad(const T *__restrict__ x, T *__restrict__ xi, int nc, int b, int ncp) {
+    const long long total = (long long)b * ncp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ncp), q = (int)(i / ncp);
+        xi[i] = c < nc ? x[(size_t)q * nc + c] : T(0);
+    }
+}
+
+template <typename T>
+__global__ void k_comp_unpad(const T *__restrict__ xi, T *__restrict__ x, int nc, int b, int ncp) {
+    const long long total = (long long)b * nc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % nc), q = (int)(i / nc);
+        x[i] = xi[(size_t)q * ncp + c];
+    }
+}
+
+inline int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 64) g = 152LL * 64;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T>
+MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T *x, T *y, T *c) {
+    const MvPlan &P = h->mv[dir];
+    MvArgs<T> a;
+    a.main = main;
+    a.dotv = dotv;
+    a.x = x;
+    a.y = y;
+    a.c = c;
+    a.nbr = P.nbr;
+    a.slot_mask = P.slot_mask;
+    a.grp_rows = P.grp_rows;
+    a.row_off = P.row_off;
+    a.pslot_slot = P.pslot_slot;
+    a.pat_ptr = P.pat_ptr;
+    a.pat_idx = P.pat_idx;
+    a.desc = P.desc;
+    a.tile_len = P.tile_len;
+    a.n_tiles = h->n_tiles;
+    a.n_slots = P.n_slots;
+    a.n_pslots = P.n_pslots;
+    a.n_groups = P.n_groups;
+    a.b = h->b;
+    a.ncp = h->ncp;
+    a.nnz_d = h->nnz_d;
+    return a;
+}
+
+template <typename T>
+sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
+    const int wpb = 4;
+    if (a.n_pslots > 0) {
+        const long long warps = (long long)a.n_tiles * a.n_pslots;
+        k_pair_dots<T><<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(a);
+        STS_LAUNCHED();
+    }
+    const long long warps = (long long)a.n_tiles * a.n_groups;
+    k_mv_main<T><<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(a);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+}  // namespace
+
+sts_status mv_repack(sts_jac_s *h, int dir, const double *S, const double *U, const double *V) {
+    MvPlan &P = h->mv[dir];
+    const double *AX = dir == 0 ? U : V;   // axpy vectors
+    const double *DV = dir == 0 ? V : U;   // dot vectors
+    const long long nm = (long long)h->n_tiles * P.tile_len * kTile;
+    const long long nd = (long long)h->n_tiles * P.n_pslots * h->b * kTile;
+    if (P.main64) {
+        k_repack_main<double><<<grid_for(nm, 256), 256, 0, h->stream>>>(
+            P.main64, S, AX, P.blk, h->d_soff, h->d_pbase, P.pos_kind, P.pos_arg, P.pat_src,
+            P.pslot_slot, P.pslot_local, P.tile_len, h->n_tiles, P.n_slots, h->b);
+        STS_LAUNCHED();
+    }
+    if (P.main32) {
+        k_repack_main<float><<<grid_for(nm, 256), 256, 0, h->stream>>>(
+            P.main32, S, AX, P.blk, h->d_soff, h->d_pbase, P.pos_kind, P.pos_arg, P.pat_src,
+            P.pslot_slot, P.pslot_local, P.tile_len, h->n_tiles, P.n_slots, h->b);
+        STS_LAUNCHED();
+    }
+    if (nd > 0 && P.dotv64) {
+        k_repack_dots<double><<<grid_for(nd, 256), 256, 0, h->stream>>>(
+            P.dotv64, DV, P.blk, h->d_pbase, P.pslot_slot, P.pslot_local, h->n_tiles, P.n_slots,
+            P.n_pslots, h->b);
+        STS_LAUNCHED();
+    }
+    if (nd > 0 && P.dotv32) {
+        k_repack_dots<float><<<grid_for(nd, 256), 256, 0, h->stream>>>(
+            P.dotv32, DV, P.blk, h->d_pbase, P.pslot_slot, P.pslot_local, h->n_tiles, P.n_slots,
+            P.n_pslots, h->b);
+        STS_LAUNCHED();
+    }
+    return STS_OK;
+}
+
+sts_status mv_apply64(sts_jac_s *h, int dir, const double *x, double *y, double *c) {
+    const MvPlan &P = h->mv[dir];
+    return mv_launch<double>(h, make_args<double>(h, dir, P.main64, P.dotv64, x, y, c));
+}
+
+sts_status mv_dots64(sts_jac_s *h, int dir, const double *x, double *c) {
+    const MvPlan &P = h->mv[dir];
+    MvArgs<double> a = make_args<double>(h, dir, P.main64, P.dotv64, x, nullptr, c);
+    if (a.n_pslots == 0) return STS_OK;
+    const long long warps = (long long)a.n_tiles * a.n_pslots;
+    k_pair_dots<double><<<(unsigned)((warps + 3) / 4), 128, 0, h->stream>>>(a);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+sts_status mv_apply32(sts_jac_s *h, int dir, const float *x, float *y, float *c) {
+    const MvPlan &P = h->mv[dir];
+    return mv_launch<float>(h, make_args<float>(h, dir, P.main32, P.dotv32, x, y, c));
+}
+
+template <typename T>
+static sts_status to_internal(sts_jac_s *h, const T *x, T *xi) {
+    if (h->layout == STS_LAYOUT_CELL_MAJOR) {
+        dim3 grid((h->ncp + 31) / 32, (h->b + 31) / 32), block(32, 8);
+        k_cell_to_comp<T><<<grid, block, 0, h->stream>>>(x, xi, h->nc, h->b, h->ncp);
+        STS_LAUNCHED();
+    } else {
+        const long long n = (long long)h->b * h->ncp;
+        k_comp_pad<T><<<grid_for(n, 256), 256, 0, h->stream>>>(x, xi, h->nc, h->b, h->ncp);
+        STS_LAUNCHED();
+    }
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+template <typename T>
+static sts_status from_internal(sts_jac_s *h, const T *xi, T *x) {
+    if (h->layout == STS_LAYOUT_CELL_MAJOR) {
+        dim3 grid((h->nc + 31) / 32, (h->b + 31) / 32), block(32, 8);
+        k_comp_to_cell<T><<<grid, block, 0, h->stream>>>(xi, x, h->nc, h->b, h->ncp);
+        STS_LAUNCHED();
+    } else {
+        const long long n = (long long)h->b * h->nc;
+        k_comp_unpad<T><<<grid_for(n, 256), 256, 0, h->stream>>>(xi, x, h->nc, h->b, h->ncp);
+        STS_LAUNCHED();
+    }
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+sts_status to_internal64(sts_jac_s *h, const double *x, double *xi) { return to_internal<double>(h, x, xi); }
+sts_status from_internal64(sts_jac_s *h, const double *xi, double *x) { return from_internal<double>(h, xi, x); }
+sts_status to_internal32(sts_jac_s *h, const float *x, float *xi) { return to_internal<float>(h, x, xi); }
+sts_status from_internal32(sts_jac_s *h, const float *xi, float *x) { return from_internal<float>(h, xi, x); }
+
+}  // namespace sts

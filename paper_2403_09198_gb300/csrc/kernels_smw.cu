@@ -1,0 +1,581 @@
+// kernels_smw.cu -- block-Jacobi through the Sherman-Morrison-Woodbury formula
+// (Section 6).  Each diagonal block is A_k = A_k^0 + U_k V_k^T with A_k^0 = S_kk
+// sparse (Eq. R1_Block_Jacobian).
+//
+// Setup, one thread per cell (lane = cell, all cells share one schedule):
+//   LU of A_k^0 without pivoting on the symbolic schedule of the shared
+//   pattern (natural order; for the paper's arrow pattern there is no fill),
+//   W_k = (A_k^0)^-1 U_k   (SMW-1, r sparse solves),
+//   C_k = I + V_k^T W_k    (FP64), C_k^-1 by Gauss-Jordan with pivoting.
+// Apply (SMW-1..3): x0 = (A_k^0)^-1 b_k, t = V_k^T x0, z = C_k^-1 t (FP64),
+//   x_k = x0 - W_k z.  The paper prints "+ W_k z"; with C_k = I + V^T A0^-1 U the
+//   Woodbury identity needs the minus sign, which is what is computed here.
+// Transposed apply: (A0 + U V^T)^-T = (A0^T + V U^T)^-1, i.e. the same steps with
+//   A0^T (solved from the same LU factors), U and V swapped and C_k^T.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "sts_internal.h"
+
+namespace sts {
+namespace {
+
+struct SetupArgs {
+    const double *Sd, *Ud, *Vd;
+    double *lu, *dinv, *W, *Wt, *Cinv;
+    const int *lu_diag, *src_slot, *d_ptr;
+    const int *colL_ptr, *colL_slot, *upd_ptr, *upd_tgt, *upd_src;
+    const int *fwd_ptr0, *fwd_col0, *fwd_slot0, *bwd_ptr0, *bwd_col0, *bwd_slot0;
+    const int *fwd_ptr1, *fwd_col1, *fwd_slot1, *bwd_ptr1, *bwd_col1, *bwd_slot1;
+    int *err_cell;
+    int nc, ncp, b, r, nnz_lu, nnz_d, with_T;
+};
+
+// Solve A0 w = rhs in place on w[q * ncp + cell] (column of W), N direction.
+__device__ void lu_solve_N(const SetupArgs &a, double *w, int cell) {
+    const size_t P = a.ncp;
+    for (int i = 0; i < a.b; ++i) {
+        double acc = w[i * P + cell];
+        for (int e = a.fwd_ptr0[i]; e < a.fwd_ptr0[i + 1]; ++e)
+            acc = fma(-a.lu[(size_t)a.fwd_slot0[e] * P + cell], w[(size_t)a.fwd_col0[e] * P + cell], acc);
+        w[i * P + cell] = acc;
+    }
+    for (int r = 0; r < a.b; ++r) {
+        const int i = a.b - 1 - r;
+        double acc = w[i * P + cell];
+        for (int e = a.bwd_ptr0[r]; e < a.bwd_ptr0[r + 1]; ++e)
+            acc = fma(-a.lu[(size_t)a.bwd_slot0[e] * P + cell], w[(size_t)a.bwd_col0[e] * P + cell], acc);
+        w[i * P + cell] = acc * a.dinv[i * P + cell];
+    }
+}
+
+// Solve A0^T w = rhs in place: U^T (forward, with the pivots), then L^T (unit).
+__device__ void lu_solve_T(const SetupArgs &a, double *w, int cell) {
+    const size_t P = a.ncp;
+    for (int i = 0; i < a.b; ++i) {
+        double acc = w[i * P + cell];
+        for (int e = a.fwd_ptr1[i]; e < a.fwd_ptr1[i + 1]; ++e)
+            acc = fma(-a.lu[(size_t)a.fwd_slot1[e] * P + cell], w[(size_t)a.fwd_col1[e] * P + cell], acc);
+        w[i * P + cell] = acc * a.dinv[i * P + cell];
+    }
+    for (int r = 0; r < a.b; ++r) {
+        const int i = a.b - 1 - r;
+        double acc = w[i * P + cell];
+        for (int e = a.bwd_ptr1[r]; e < a.bwd_ptr1[r + 1]; ++e)
+            acc = fma(-a.lu[(size_t)a.bwd_slot1[e] * P + cell], w[(size_t)a.bwd_col1[e] * P + cell], acc);
+        w[i * P + cell] = acc;
+    }
+}
+
+__global__ void k_smw_setup(SetupArgs a) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= a.ncp) return;
+    const size_t P = a.ncp;
+    const int r = a.r;
+    if (cell >= a.nc) {   // padding cell: identity block, no pairs
+        for (int s = 0; s < a.nnz_lu; ++s) a.lu[s * P + cell] = 0.0;
+        for (int i = 0; i < a.b; ++i) {
+            a.lu[(size_t)a.lu_diag[i] * P + cell] = 1.0;
+            a.dinv[i * P + cell] = 1.0;
+        }
+        for (int k = 0; k < r; ++k)
+            for (int q = 0; q < a.b; ++q) {
+                a.W[((size_t)k * a.b + q) * P + cell] = 0.0;
+                if (a.with_T) a.Wt[((size_t)k * a.b + q) * P + cell] = 0.0;
+            }
+        for (int k = 0; k < r; ++k)
+            for (int l = 0; l < r; ++l) a.Cinv[((size_t)k * r + l) * P + cell] = k == l ? 1.0 : 0.0;
+        return;
+    }
+    // 1. load S_kk into the LU slots
+    for (int s = 0; s < a.nnz_lu; ++s) a.lu[s * P + cell] = 0.0;
+    for (int e = 0; e < a.nnz_d; ++e) a.lu[(size_t)a.src_slot[e] * P + cell] = a.Sd[e * P + cell];
+    // 2. static-pivot LU on the shared schedule
+    for (int k = 0; k < a.b; ++k) {
+        double rowmax = 0.0;
+        for (int e = a.d_ptr[k]; e < a.d_ptr[k + 1]; ++e) rowmax = fmax(rowmax, fabs(a.Sd[e * P + cell]));
+        const double piv = a.lu[(size_t)a.lu_diag[k] * P + cell];
+        if (!(fabs(piv) > 1e-14 * rowmax)) {
+            atomicMin(a.err_cell, cell);
+            return;
+        }
+        const double d = 1.0 / piv;
+        a.dinv[k * P + cell] = d;
+        for (int e = a.colL_ptr[k]; e < a.colL_ptr[k + 1]; ++e) {
+            const size_t sl = (size_t)a.colL_slot[e] * P + cell;
+            const double l = a.lu[sl] * d;
+            a.lu[sl] = l;
+            for (int u = a.upd_ptr[e]; u < a.upd_ptr[e + 1]; ++u)
+                a.lu[(size_t)a.upd_tgt[u] * P + cell] =
+                    fma(-l, a.lu[(size_t)a.upd_src[u] * P + cell], a.lu[(size_t)a.upd_tgt[u] * P + cell]);
+        }
+    }
+    // 3. W = A0^-1 U (SMW-1) and, for the adjoint, Wt = A0^-T V
+    for (int k = 0; k < r; ++k) {
+        double *w = a.W + (size_t)k * a.b * P;
+        for (int q = 0; q < a.b; ++q) w[q * P + cell] = a.Ud[((size_t)k * a.b + q) * P + cell];
+        lu_solve_N(a, w, cell);
+        if (a.with_T) {
+            double *wt = a.Wt + (size_t)k * a.b * P;
+            for (int q = 0; q < a.b; ++q) wt[q * P + cell] = a.Vd[((size_t)k * a.b + q) * P + cell];
+            lu_solve_T(a, wt, cell);
+        }
+    }
+    // 4. C = I + V^T W (FP64) and its inverse (Gauss-Jordan, partial pivoting)
+    double C[kMaxPairsDiag][kMaxPairsDiag], X[kMaxPairsDiag][kMaxPairsDiag];
+    double cmax = 0.0;
+    for (int k = 0; k < r; ++k)
+        for (int l = 0; l < r; ++l) {
+            double acc = k == l ? 1.0 : 0.0;
+            for (int q = 0; q < a.b; ++q)
+                acc = fma(a.Vd[((size_t)k * a.b + q) * P + cell], a.W[((size_t)l * a.b + q) * P + cell], acc);
+            C[k][l] = acc;
+            X[k][l] = k == l ? 1.0 : 0.0;
+            cmax = fmax(cmax, fabs(acc));
+        }
+    for (int k = 0; k < r; ++k) {
+        int pr = k;
+        for (int i = k + 1; i < r; ++i)
+            if (fabs(C[i][k]) > fabs(C[pr][k])) pr = i;
+        if (!(fabs(C[pr][k]) > 1e-14 * cmax)) {
+            atomicMin(a.err_cell, cell);
+            return;
+        }
+        if (pr != k)
+            for (int j = 0; j < r; ++j) {
+                double t = C[k][j]; C[k][j] = C[pr][j]; C[pr][j] = t;
+                t = X[k][j]; X[k][j] = X[pr][j]; X[pr][j] = t;
+            }
+        const double d = 1.0 / C[k][k];
+        for (int j = 0; j < r; ++j) { C[k][j] *= d; X[k][j] *= d; }
+        for (int i = 0; i < r; ++i) {
+            if (i == k) continue;
+            const double f = C[i][k];
+            for (int j = 0; j < r; ++j) { C[i][j] -= f * C[k][j]; X[i][j] -= f * X[k][j]; }
+        }
+    }
+    for (int k = 0; k < r; ++k)
+        for (int l = 0; l < r; ++l) a.Cinv[((size_t)k * r + l) * P + cell] = X[k][l];
+}
+
+// Write the apply streams: forward coefficients, then per backward row its
+// pivot inverse followed by its coefficients (scaled by the row's dinv where the
+// program asks for it).
+template <typename T>
+__global__ void k_smw_pack(T *out, const double *lu, const double *dinv, const int *pk_slot,
+                           const int *pk_scale, int len, int ncp) {
+    const long long total = (long long)len * ncp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cell = (int)(i % ncp), pos = (int)(i / ncp);
+        const int sl = pk_slot[pos], sc = pk_scale[pos];
+        double v;
+        if (sl >= 0) {
+            v = lu[(size_t)sl * ncp + cell];
+            if (sc >= 0) v *= dinv[(size_t)sc * ncp + cell];
+        } else {
+            v = dinv[(size_t)sc * ncp + cell];
+        }
+        out[i] = (T)v;
+    }
+}
+
+template <typename T>
+__global__ void k_round(T *out, const double *in, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+template <typename T>
+struct ApplyArgs {
+    const T *st;            // [len][ncp] stream
+    const unsigned *desc;   // [len] apply program
+    const T *dv;            // [r][b][ncp] dot vectors (V for N, U for T)
+    const T *W;             // [r][b][ncp] (W for N, Wt for T)
+    const double *Cinv;     // [r][r][ncp]
+    const T *x;
+    T *y;
+    int len, b, r, ncp, trans;
+};
+
+template <typename T> struct ApChunk { static constexpr int CH = 8; };
+template <> struct ApChunk<float> { static constexpr int CH = 16; };
+
+// One warp per 32 cells, one lane per cell; the working vector lives in
+// shared memory [q][lane].  The triangular sweeps run a flat program (one
+// descriptor per stream position) while the stream is double-buffered in
+// registers, so each lane has the next chunk's loads in flight.
+template <typename T, int RMAX>
+__global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
+    constexpr int CH = ApChunk<T>::CH;
+    extern __shared__ unsigned char smem_raw[];
+    T *w = reinterpret_cast<T *>(smem_raw);
+    const int lane = threadIdx.x;
+    const int cell = blockIdx.x * kTile + lane;
+    const size_t P = a.ncp;
+    const T *__restrict__ x = a.x;
+    for (int i = 0; i < a.b; ++i) w[i * kTile + lane] = __ldg(x + i * P + cell);
+    const T *__restrict__ st = a.st + cell;
+    const unsigned *__restrict__ dd = a.desc;
+    const int L = a.len;
+    T cur[CH], nxt[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) cur[i] = i < L ? __ldg(st + (size_t)i * P) : T(0);
+    T acc = T(0);
+    for (int base = 0; base < L; base += CH) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int pp = base + CH + i;
+            nxt[i] = pp < L ? __ldg(st + (size_t)pp * P) : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int pp = base + i;
+            if (pp < L) {
+                const unsigned d = __ldg(dd + pp);
+                const int row = (d >> 12) & 0xfffu, col = d & 0xfffu;
+                if (d & kApScale) {
+                    acc = cur[i] * w[row * kTile + lane];
+                } else {
+                    if (d & kApBegin) acc = w[row * kTile + lane];
+                    acc = fma(-cur[i], w[col * kTile + lane], acc);
+                }
+                if (d & kApEnd) w[row * kTile + lane] = acc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) cur[i] = nxt[i];
+    }
+    // t = dv^T x0, z = C^-1 t (FP64), x = x0 - W z
+    T t[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) t[k] = T(0);
+    const T *__restrict__ dv = a.dv + cell;
+#pragma unroll 4
+    for (int q = 0; q < a.b; ++q) {
+        const T xq = w[q * kTile + lane];
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k)
+            if (k < a.r) t[k] = fma(__ldg(dv + ((size_t)k * a.b + q) * P), xq, t[k]);
+    }
+    T z[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+        double s = 0.0;
+        if (k < a.r) {
+#pragma unroll
+            for (int l = 0; l < RMAX; ++l)
+                if (l < a.r) {
+                    const double cij = a.trans ? __ldg(a.Cinv + ((size_t)l * a.r + k) * P + cell)
+                                               : __ldg(a.Cinv + ((size_t)k * a.r + l) * P + cell);
+                    s = fma(cij, (double)t[l], s);
+                }
+        }
+        z[k] = (T)s;
+    }
+    const T *__restrict__ Wp = a.W + cell;
+#pragma unroll 4
+    for (int q = 0; q < a.b; ++q) {
+        T v = w[q * kTile + lane];
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k)
+            if (k < a.r) v = fma(-__ldg(Wp + ((size_t)k * a.b + q) * P), z[k], v);
+        a.y[q * P + cell] = v;
+    }
+}
+
+// Repack diagonal-block values into [entry][cell] and the diagonal pairs into [k][q][cell].
+__global__ void k_smw_repack(double *Sd, double *Ud, double *Vd, const double *S, const double *U,
+                             const double *V, const int *diag_blk, const long long *soff,
+                             const int *pbase, int nc, int ncp, int nnz_d, int b, int r) {
+    const long long nS = (long long)nnz_d * ncp, nP = (long long)r * b * ncp;
+    const long long total = nS + nP;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < nS) {
+            const int cell = (int)(i % ncp), e = (int)(i / ncp);
+            Sd[i] = cell < nc ? S[soff[diag_blk[cell]] + e] : 0.0;
+        } else {
+            const long long j = i - nS;
+            const int cell = (int)(j % ncp);
+            const long long kq = j / ncp;
+            const int q = (int)(kq % b), k = (int)(kq / b);
+            double u = 0.0, v = 0.0;
+            if (cell < nc) {
+                const size_t src = (size_t)(pbase[diag_blk[cell]] + k) * b + q;
+                u = U[src];
+                v = V[src];
+            }
+            Ud[j] = u;
+            Vd[j] = v;
+        }
+    }
+}
+
+inline int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 64) g = 152LL * 64;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// Host: symbolic factorisation of the shared diagonal pattern and the programs
+// of the two apply directions.
+sts_status smw_build(sts_jac_s *h) {
+    SmwPlan &M = h->smw;
+    const int b = h->b;
+    if (b > 4095) return set_error(STS_ERR_INVALID_ARG, "block_size above 4095 is not supported by the SMW apply");
+    if (h->r_diag > kMaxPairsDiag)
+        return set_error(STS_ERR_INVALID_ARG, "r_diag = %d exceeds the supported %d pairs per diagonal block",
+                         h->r_diag, kMaxPairsDiag);
+    std::vector<char> nz((size_t)b * b, 0);
+    for (int p = 0; p < b; ++p)
+        for (int e = h->dptr[p]; e < h->dptr[p + 1]; ++e) nz[(size_t)p * b + h->didx[e]] = 1;
+    for (int k = 0; k < b; ++k)               // symbolic elimination, natural order
+        for (int i = k + 1; i < b; ++i)
+            if (nz[(size_t)i * b + k])
+                for (int j = k + 1; j < b; ++j)
+                    if (nz[(size_t)k * b + j]) nz[(size_t)i * b + j] = 1;
+    std::vector<int> slot((size_t)b * b, -1);
+    M.h_lu_ptr.assign(b + 1, 0);
+    M.h_lu_idx.clear();
+    M.h_lu_diag.assign(b, -1);
+    for (int i = 0; i < b; ++i) {
+        for (int j = 0; j < b; ++j)
+            if (nz[(size_t)i * b + j]) {
+                slot[(size_t)i * b + j] = (int)M.h_lu_idx.size();
+                if (i == j) M.h_lu_diag[i] = (int)M.h_lu_idx.size();
+                M.h_lu_idx.push_back(j);
+            }
+        M.h_lu_ptr[i + 1] = (int)M.h_lu_idx.size();
+    }
+    M.nnz_lu = (int)M.h_lu_idx.size();
+    M.h_src_slot.assign(h->nnz_d, 0);
+    for (int p = 0; p < b; ++p)
+        for (int e = h->dptr[p]; e < h->dptr[p + 1]; ++e) M.h_src_slot[e] = slot[(size_t)p * b + h->didx[e]];
+    // factorisation schedule
+    std::vector<int> colL_ptr(b + 1, 0), colL_slot, upd_ptr(1, 0), upd_tgt, upd_src;
+    for (int k = 0; k < b; ++k) {
+        for (int i = k + 1; i < b; ++i) {
+            if (slot[(size_t)i * b + k] < 0) continue;
+            colL_slot.push_back(slot[(size_t)i * b + k]);
+            for (int j = k + 1; j < b; ++j)
+                if (slot[(size_t)k * b + j] >= 0) {
+                    upd_tgt.push_back(slot[(size_t)i * b + j]);
+                    upd_src.push_back(slot[(size_t)k * b + j]);
+                }
+            upd_ptr.push_back((int)upd_tgt.size());
+        }
+        colL_ptr[k + 1] = (int)colL_slot.size();
+    }
+    // apply programs.  dir 0 (A0):  forward  L rows   (i, j<i), coefficient L_ij
+    //                               backward U rows   (i, j>i), coefficient U_ij * dinv_i
+    //                  dir 1 (A0^T): forward  U cols   (j<i, i), coefficient U_ji * dinv_j
+    //                               backward L cols   (j>i, i), coefficient L_ji
+    // Setup solves use the unscaled LU slots with the same row lists.
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<int> fptr(b + 1, 0), fcol, fslot, fscale, bptr(b + 1, 0), bcol, bslot, bscale;
+        // the setup's unscaled solves use (fcol, fslot) and (bcol, bslot); the
+        // apply streams carry the scaled coefficients described by (fscale, bscale)
+        for (int i = 0; i < b; ++i) {
+            for (int j = 0; j < i; ++j) {
+                const int sl = dir == 0 ? slot[(size_t)i * b + j] : slot[(size_t)j * b + i];
+                if (sl < 0) continue;
+                fcol.push_back(j);
+                fslot.push_back(sl);
+                fscale.push_back(dir == 0 ? -1 : j);
+            }
+            fptr[i + 1] = (int)fcol.size();
+        }
+        for (int r = 0; r < b; ++r) {
+            const int i = b - 1 - r;
+            for (int j = i + 1; j < b; ++j) {
+                const int sl = dir == 0 ? slot[(size_t)i * b + j] : slot[(size_t)j * b + i];
+                if (sl < 0) continue;
+                bcol.push_back(j);
+                bslot.push_back(sl);
+                bscale.push_back(dir == 0 ? i : -1);
+            }
+            bptr[r + 1] = (int)bcol.size();
+        }
+        M.n_fwd[dir] = (int)fcol.size();
+        M.n_bwd[dir] = (int)bcol.size();
+        // pack tables: stream = forward entries, then per backward row [dinv_i, entries...]
+        std::vector<int> pk_slot, pk_scale;
+        for (size_t e = 0; e < fcol.size(); ++e) {
+            pk_slot.push_back(fslot[e]);
+            pk_scale.push_back(fscale[e]);
+        }
+        for (int r = 0; r < b; ++r) {
+            const int i = b - 1 - r;
+            pk_slot.push_back(-1);
+            pk_scale.push_back(i);
+            for (int e = bptr[r]; e < bptr[r + 1]; ++e) {
+                pk_slot.push_back(bslot[e]);
+                pk_scale.push_back(bscale[e]);
+            }
+        }
+        STS_TRY(upload(h, &M.ap_fwd_ptr[dir], fptr));
+        STS_TRY(upload(h, &M.ap_fwd_col[dir], fcol));
+        STS_TRY(upload(h, &M.ap_fwd_slot[dir], fslot));
+        STS_TRY(upload(h, &M.ap_bwd_ptr[dir], bptr));
+        STS_TRY(upload(h, &M.ap_bwd_col[dir], bcol));
+        STS_TRY(upload(h, &M.ap_bwd_slot[dir], bslot));
+        STS_TRY(upload(h, &M.pk_slot[dir], pk_slot));
+        STS_TRY(upload(h, &M.pk_scale[dir], pk_scale));
+        // apply program, same position order as the pack tables
+        std::vector<unsigned> desc;
+        for (int i = 0; i < b; ++i)
+            for (int e = fptr[i]; e < fptr[i + 1]; ++e) {
+                unsigned d = (unsigned)fcol[e] | ((unsigned)i << 12);
+                if (e == fptr[i]) d |= kApBegin;
+                if (e == fptr[i + 1] - 1) d |= kApEnd;
+                desc.push_back(d);
+            }
+        for (int r = 0; r < b; ++r) {
+            const int i = b - 1 - r;
+            desc.push_back(((unsigned)i << 12) | kApScale | (bptr[r + 1] == bptr[r] ? kApEnd : 0u));
+            for (int e = bptr[r]; e < bptr[r + 1]; ++e) {
+                unsigned d = (unsigned)bcol[e] | ((unsigned)i << 12);
+                if (e == bptr[r + 1] - 1) d |= kApEnd;
+                desc.push_back(d);
+            }
+        }
+        if (desc.size() != pk_slot.size()) return set_error(STS_ERR_INVALID_ARG, "internal: apply program size");
+        STS_TRY(upload(h, &M.ap_desc[dir], desc));
+    }
+    STS_TRY(upload(h, &M.lu_diag, M.h_lu_diag));
+    STS_TRY(upload(h, &M.src_slot, M.h_src_slot));
+    STS_TRY(upload(h, &M.d_ptr, h->dptr));
+    STS_TRY(upload(h, &M.f_colL_ptr, colL_ptr));
+    STS_TRY(upload(h, &M.f_colL_slot, colL_slot));
+    STS_TRY(upload(h, &M.f_upd_ptr, upd_ptr));
+    STS_TRY(upload(h, &M.f_upd_tgt, upd_tgt));
+    STS_TRY(upload(h, &M.f_upd_src, upd_src));
+    const size_t P = h->ncp;
+    const int r = h->r_diag;
+    STS_TRY(dalloc(h, &M.Sd, (size_t)h->nnz_d * P));
+    STS_TRY(dalloc(h, &M.Ud, (size_t)std::max(r, 1) * b * P));
+    STS_TRY(dalloc(h, &M.Vd, (size_t)std::max(r, 1) * b * P));
+    STS_TRY(dalloc(h, &M.lu, (size_t)M.nnz_lu * P));
+    STS_TRY(dalloc(h, &M.dinv, (size_t)b * P));
+    STS_TRY(dalloc(h, &M.W, (size_t)std::max(r, 1) * b * P));
+    if (h->has_T) STS_TRY(dalloc(h, &M.Wt, (size_t)std::max(r, 1) * b * P));
+    STS_TRY(dalloc(h, &M.Cinv, (size_t)std::max(r * r, 1) * P));
+    for (int dir = 0; dir < 2; ++dir) {
+        if (dir == 1 && !h->has_T) continue;
+        const size_t len = (size_t)M.n_fwd[dir] + M.n_bwd[dir] + b;
+        STS_TRY(dalloc(h, &M.ap64[dir], len * P));
+        if (h->dtype == STS_MIXED) {
+            STS_TRY(dalloc(h, &M.ap32[dir], len * P));
+            STS_TRY(dalloc(h, &M.W32[dir], (size_t)std::max(r, 1) * b * P));
+            STS_TRY(dalloc(h, &M.DV32[dir], (size_t)std::max(r, 1) * b * P));
+        }
+    }
+    STS_TRY(dalloc(h, &M.err_cell, 1));
+    std::vector<int> diag_blk(h->nc);
+    for (int c = 0; c < h->nc; ++c)
+        for (int k = h->bptr[c]; k < h->bptr[c + 1]; ++k)
+            if (h->bidx[k] == c) diag_blk[c] = k;
+    STS_TRY(upload(h, &M.diag_blk, diag_blk));
+    return STS_OK;
+}
+
+sts_status smw_repack(sts_jac_s *h, const double *S, const double *U, const double *V) {
+    SmwPlan &M = h->smw;
+    M.ready = false;
+    const long long total = (long long)h->nnz_d * h->ncp + (long long)h->r_diag * h->b * h->ncp;
+    k_smw_repack<<<grid_for(total, 256), 256, 0, h->stream>>>(
+        M.Sd, M.Ud, M.Vd, S, U, V, M.diag_blk, h->d_soff, h->d_pbase, h->nc, h->ncp, h->nnz_d,
+        h->b, h->r_diag);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+sts_status smw_setup(sts_jac_s *h) {
+    SmwPlan &M = h->smw;
+    M.ready = false;
+    SetupArgs a;
+    a.Sd = M.Sd; a.Ud = M.Ud; a.Vd = M.Vd;
+    a.lu = M.lu; a.dinv = M.dinv; a.W = M.W; a.Wt = M.Wt; a.Cinv = M.Cinv;
+    a.lu_diag = M.lu_diag; a.src_slot = M.src_slot; a.d_ptr = M.d_ptr;
+    a.colL_ptr = M.f_colL_ptr; a.colL_slot = M.f_colL_slot;
+    a.upd_ptr = M.f_upd_ptr; a.upd_tgt = M.f_upd_tgt; a.upd_src = M.f_upd_src;
+    a.fwd_ptr0 = M.ap_fwd_ptr[0]; a.fwd_col0 = M.ap_fwd_col[0]; a.fwd_slot0 = M.ap_fwd_slot[0];
+    a.bwd_ptr0 = M.ap_bwd_ptr[0]; a.bwd_col0 = M.ap_bwd_col[0]; a.bwd_slot0 = M.ap_bwd_slot[0];
+    a.fwd_ptr1 = M.ap_fwd_ptr[1]; a.fwd_col1 = M.ap_fwd_col[1]; a.fwd_slot1 = M.ap_fwd_slot[1];
+    a.bwd_ptr1 = M.ap_bwd_ptr[1]; a.bwd_col1 = M.ap_bwd_col[1]; a.bwd_slot1 = M.ap_bwd_slot[1];
+    a.err_cell = M.err_cell;
+    a.nc = h->nc; a.ncp = h->ncp; a.b = h->b; a.r = h->r_diag; a.nnz_lu = M.nnz_lu;
+    a.nnz_d = h->nnz_d; a.with_T = h->has_T ? 1 : 0;
+    const int big = INT_MAX;
+    STS_CK(cudaMemcpyAsync(M.err_cell, &big, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    k_smw_setup<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
+    STS_LAUNCHED();
+    int bad = INT_MAX;
+    STS_CK(cudaMemcpyAsync(&bad, M.err_cell, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    STS_CK(cudaStreamSynchronize(h->stream));
+    if (bad != INT_MAX)
+        return set_error(STS_ERR_SINGULAR,
+                         "block-Jacobi setup: cell %d has a pivot below 1e-14 x its row maximum "
+                         "(static pivot order) or a singular capacitance matrix C_k", bad);
+    const size_t P = h->ncp;
+    const int b = h->b, r = h->r_diag;
+    for (int dir = 0; dir < 2; ++dir) {
+        if (dir == 1 && !h->has_T) continue;
+        const int len = M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const long long n = (long long)len * P;
+        k_smw_pack<double><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, M.pk_slot[dir],
+                                                                     M.pk_scale[dir], len, h->ncp);
+        STS_LAUNCHED();
+        if (M.ap32[dir]) {
+            k_smw_pack<float><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap32[dir], M.lu, M.dinv, M.pk_slot[dir],
+                                                                       M.pk_scale[dir], len, h->ncp);
+            STS_LAUNCHED();
+            const long long nw = (long long)r * b * P;
+            if (nw > 0) {
+                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.W32[dir], dir == 0 ? M.W : M.Wt, nw);
+                STS_LAUNCHED();
+                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.DV32[dir], dir == 0 ? M.Vd : M.Ud, nw);
+                STS_LAUNCHED();
+            }
+        }
+    }
+    M.ready = true;
+    return STS_OK;
+}
+
+template <typename T>
+static sts_status smw_apply_t(sts_jac_s *h, int dir, const T *st, const T *dv, const T *W, const T *x,
+                              T *z) {
+    const SmwPlan &M = h->smw;
+    ApplyArgs<T> a;
+    a.st = st; a.desc = M.ap_desc[dir]; a.dv = dv; a.W = W; a.Cinv = M.Cinv; a.x = x; a.y = z;
+    a.len = M.n_fwd[dir] + M.n_bwd[dir] + h->b; a.b = h->b; a.r = h->r_diag; a.ncp = h->ncp; a.trans = dir;
+    const size_t smem = (size_t)h->b * kTile * sizeof(T);
+    auto kern = a.r <= 2 ? k_smw_apply<T, 2> : a.r <= 4 ? k_smw_apply<T, 4> : k_smw_apply<T, kMaxPairsDiag>;
+    if (smem > 48 * 1024)
+        STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<h->n_tiles, kTile, smem, h->stream>>>(a);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+sts_status smw_apply64(sts_jac_s *h, int dir, const double *x, double *z) {
+    const SmwPlan &M = h->smw;
+    return smw_apply_t<double>(h, dir, M.ap64[dir], dir == 0 ? M.Vd : M.Ud, dir == 0 ? M.W : M.Wt, x, z);
+}
+
+sts_status smw_apply32(sts_jac_s *h, int dir, const float *x, float *z) {
+    const SmwPlan &M = h->smw;
+    return smw_apply_t<float>(h, dir, M.ap32[dir], M.DV32[dir], M.W32[dir], x, z);
+}
+
+}  // namespace sts

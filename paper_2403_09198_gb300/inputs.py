@@ -207,18 +207,21 @@ def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
     rhs = _standard_normal(rng, nc * b)
     W = rng.uniform(0.5, 1.5, size=nc * b)
 
-    # interleave the two S streams into block order
-    sizes = np.where(is_diag, nnz_d, nnz_o).astype(np.int64)
-    offs = np.zeros(nnzb + 1, dtype=np.int64)
-    np.cumsum(sizes, out=offs[1:])
-    S = np.empty(int(offs[-1]), dtype=np.float64)
-    diag_blocks = np.flatnonzero(is_diag)
-    off_blocks = np.flatnonzero(~is_diag)
-    S_d_idx = offs[diag_blocks][:, None] + np.arange(nnz_d)[None, :]
-    S[S_d_idx.ravel()] = sd.ravel()
-    if n_off:
-        S_o_idx = offs[off_blocks][:, None] + np.arange(nnz_o)[None, :]
-        S[S_o_idx.ravel()] = so.ravel()
+    # interleave the two S streams into block order, one block row at a time
+    S = np.empty(nc * nnz_d + n_off * nnz_o, dtype=np.float64)
+    pos = 0
+    o = 0
+    cols = block_indices
+    for i in range(nc):
+        for k in range(int(block_indptr[i]), int(block_indptr[i + 1])):
+            if cols[k] == i:
+                S[pos:pos + nnz_d] = sd[i]
+                pos += nnz_d
+            else:
+                S[pos:pos + nnz_o] = so[o]
+                pos += nnz_o
+                o += 1
+    assert pos == S.shape[0] and o == n_off
 
     return Workload(Lx=Lx, Ly=Ly, N=N, b=b, r_diag=r_diag, r_off=r_off,
                     block_indptr=block_indptr, block_indices=block_indices,

@@ -1,0 +1,382 @@
+"""Parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Small workloads are compared element by element on whole outputs; the
+128 x 128, N = 60 and 256 x 256, N = 200 workloads are compared on sampled
+outputs the oracle computes one by one, in the launch configuration the
+benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_09198_gb300 import inputs
+from paper_2403_09198_gb300.binding import StsError, StsJacobian
+from tests._gpu import (SMALL, TOL64, dev, from_component_major, host, oracle_jac, rel_err,
+                        to_component_major, workload)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _jac(w, **kw):
+    return StsJacobian(w, dev(w.S), dev(w.U), dev(w.V), **kw)
+
+
+# ---------------------------------------------------------------- matvec
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("layout", ["cell", "component"])
+def test_matvec_small(name, layout):
+    w = workload(name)
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True, layout=layout)
+    x = np.random.default_rng(1).standard_normal(w.n)
+    for trans in (False, True):
+        ref = oracle.matvec(J, x, trans=trans)
+        if layout == "cell":
+            got = host(jac.matvec(dev(x), trans=trans))
+        else:
+            got = from_component_major(
+                host(jac.matvec(dev(to_component_major(x, w.n_cells, w.b)), trans=trans)),
+                w.n_cells, w.b)
+        assert rel_err(got, ref) <= TOL64, (name, trans)
+    jac.close()
+
+
+def test_matvec_worked_example_bit_exact():
+    """Section 5.1 r1-sparse example on one cell: integer x keeps every product
+    exact, so the GPU result equals the oracle bit for bit."""
+    from tests._golden import load
+    g, r1 = load("csr_example"), load("r1_sparse_example")
+
+    class W:
+        b = 4
+        block_indptr = np.array([0, 1])
+        block_indices = np.array([0])
+        d_indptr = np.array(g["indptr"])
+        d_indices = np.array(g["indices"])
+        o_indptr = np.zeros(5, dtype=np.int32)
+        o_indices = np.zeros(0, dtype=np.int32)
+        r_diag, r_off = 2, 0
+        pair_indptr = np.array([0, 2])
+        S = np.array(g["data"], dtype=float)
+        U = np.array(r1["r1_columns"], dtype=float)
+        V = np.array(r1["r1_rows"], dtype=float)
+
+    jac = StsJacobian(W, dev(W.S), dev(W.U), dev(W.V), transpose=True)
+    J = oracle.Jacobian.from_workload(W)
+    for x in ([1.0, -2.0, 3.0, 5.0], [0.0, 0.0, 0.0, 1.0]):
+        x = np.array(x)
+        for trans in (False, True):
+            assert np.array_equal(host(jac.matvec(dev(x), trans=trans)), oracle.matvec(J, x, trans=trans))
+
+
+def _sample_rows(w, rng, n_rand=3000):
+    nc, b = w.n_cells, w.b
+    special = [0, w.Lx - 1, nc - w.Lx, nc - 1, nc // 2]
+    rows = [c * b + p for c in special for p in range(b)]
+    rows += list(rng.choice(nc * b, n_rand, replace=False))
+    return np.unique(np.array(rows, dtype=np.int64))
+
+
+@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200"])
+def test_matvec_full_size_sampled(name):
+    w = inputs.named_workload(name)
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=(name == "grid128_N60"), layout="component")
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(w.n)
+    rows = _sample_rows(w, rng)
+    xi = to_component_major(x, w.n_cells, w.b)
+    for trans in ((False, True) if name == "grid128_N60" else (False,)):
+        y = from_component_major(host(jac.matvec(dev(xi), trans=trans)), w.n_cells, w.b)
+        ref = oracle.matvec_rows(J, x, rows, trans=trans)
+        assert rel_err(y[rows], ref) <= TOL64, trans
+    jac.close()
+
+
+# ---------------------------------------------------------------- block-Jacobi
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_bjacobi_small(name):
+    w = workload(name)
+    J = oracle_jac(w)
+    F = oracle.bj_setup(J)
+    jac = _jac(w, transpose=True)
+    jac.bjacobi_setup()
+    x = np.random.default_rng(2).standard_normal(w.n)
+    for trans in (False, True):
+        got = host(jac.bjacobi_apply(dev(x), trans=trans))
+        assert rel_err(got, oracle.bj_apply(F, x, trans=trans)) <= TOL64, (name, trans)
+    jac.close()
+
+
+def test_bjacobi_full_size_sampled():
+    w = inputs.named_workload("grid128_N60")
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True, layout="component")
+    jac.bjacobi_setup()
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(w.n)
+    cells = np.unique(np.concatenate([[0, 127, w.n_cells - 1], rng.choice(w.n_cells, 300, replace=False)]))
+    xi = dev(to_component_major(x, w.n_cells, w.b))
+    for trans in (False, True):
+        z = from_component_major(host(jac.bjacobi_apply(xi, trans=trans)), w.n_cells, w.b)
+        ref = oracle.bj_cells(J, x, cells, trans=trans)
+        got = z.reshape(w.n_cells, w.b)[cells]
+        assert rel_err(got, ref) <= TOL64, trans
+    jac.close()
+
+
+def test_bjacobi_errors():
+    w = workload("ragged5x3")
+    jac = _jac(w)
+    with pytest.raises(StsError) as e:
+        jac.bjacobi_apply(dev(np.zeros(w.n)))
+    assert e.value.status == 8                     # STS_ERR_NOT_SETUP
+    S = w.S.copy()
+    offs = w.s_offsets()
+    k = np.flatnonzero(w.is_diag_block())[7]       # cell 7
+    S[offs[k]:offs[k + 1]] = 0.0
+    jac.update_values(dev(S), dev(w.U), dev(w.V))
+    with pytest.raises(StsError) as e:
+        jac.bjacobi_setup()
+    assert e.value.status == 4 and "cell 7" in e.value.message
+    jac.close()
+
+
+# ---------------------------------------------------------------- GMRES
+
+
+@pytest.mark.parametrize("case", ["grid16_N10", "weak_diag_restart"])
+def test_gmres_parity(case):
+    if case == "grid16_N10":
+        w, m = workload("grid16_N10"), 20
+    else:
+        w, m = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 4
+    J = oracle_jac(w)
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    xg, ig = jac.gmres(dev(w.rhs), restart=m, rtol=1e-10, history=True)
+    xo, io = oracle.gmres(J, w.rhs, restart=m, rtol=1e-10)
+    assert ig.converged and io["converged"]
+    assert ig.true_rel_residual <= 1e-10 and io["true_rel"] <= 1e-10
+    r = w.rhs - oracle.matvec(J, host(xg))
+    assert np.linalg.norm(r) / np.linalg.norm(w.rhs) <= 1e-10
+    assert abs(ig.iterations - io["iterations"]) <= 1
+    ho = np.array(io["history"])
+    n = min(len(ho), len(ig.history))
+    keep = ho[:n] > 1e-13
+    # 1e-8 relative while the residual is above 1e-13, plus an absolute floor
+    # of 1e-18 (in units of ||b||), far below the rounding level of either solver
+    np.testing.assert_allclose(ig.history[:n][keep], ho[:n][keep], rtol=1e-8, atol=1e-18)
+    xg2, _ = jac.gmres(dev(w.rhs), restart=m, rtol=1e-14, max_iters=400)
+    xo2, _ = oracle.gmres(J, w.rhs, restart=m, rtol=1e-14, max_iters=400)
+    assert np.linalg.norm(host(xg2) - xo2) / np.linalg.norm(xo2) <= TOL64
+    jac.close()
+
+
+def test_gmres_host_vectors_transposed_and_unpreconditioned():
+    w = workload("ragged5x3")
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(w.rhs.copy(), rtol=1e-12)                 # host vectors
+    assert isinstance(x, np.ndarray) and info.converged
+    assert rel_err(x, oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
+    xt, it = jac.gmres(dev(w.rhs), rtol=1e-12, trans=True)
+    assert it.converged
+    assert rel_err(host(xt), oracle.gmres(J, w.rhs, rtol=1e-14, trans=True)[0]) <= 1e-10
+    xn, inn = jac.gmres(dev(w.rhs), rtol=1e-12, precond="none", restart=60)
+    assert inn.converged
+    assert rel_err(host(xn), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
+    jac.close()
+
+
+def test_gmres_not_converged_keeps_x():
+    w = inputs.make_workload(6, 5, N=4, w=2, seed=9, dt=0.5)
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), rtol=1e-14, max_iters=1, raise_on_fail=False)
+    assert not info.converged and info.iterations == 1
+    r = w.rhs - oracle.matvec(oracle_jac(w), host(x))
+    assert abs(np.linalg.norm(r) / np.linalg.norm(w.rhs) - info.true_rel_residual) <= 1e-12
+    with pytest.raises(StsError) as e:
+        jac.gmres(dev(w.rhs), rtol=1e-14, max_iters=1)
+    assert e.value.status == 5
+    jac.close()
+
+
+def test_gmres_zero_rhs():
+    w = workload("ragged5x3")
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(np.zeros(w.n)))
+    assert info.converged and info.iterations == 0 and not host(x).any()
+
+
+def test_gmres_full_size_true_residual():
+    """128 x 128, N = 60: GMRES(30) to 1e-10; the oracle recomputes the residual
+    of the GPU solution and solves the same system for the iteration count."""
+    w = inputs.named_workload("grid128_N60")
+    J = oracle_jac(w)
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), restart=30, rtol=1e-10, history=True)
+    r = w.rhs - oracle.matvec(J, host(x))
+    assert info.converged and np.linalg.norm(r) / np.linalg.norm(w.rhs) <= 1e-10
+    xo, io = oracle.gmres(J, w.rhs, restart=30, rtol=1e-10)
+    assert abs(info.iterations - io["iterations"]) <= 1
+    jac.close()
+
+
+# ---------------------------------------------------------------- mixed precision
+
+
+def test_mixed_precision_fgmres():
+    """FP32 matvec and block-Jacobi inside FP64 flexible GMRES: the true FP64
+    residual reaches 1e-10 and the error against the FP64 oracle stays within
+    kappa(J) * 1e-10 (kappa from numpy on this small system)."""
+    w = inputs.make_workload(8, 8, N=10, w=2, seed=13)
+    J = oracle_jac(w)
+    jac = _jac(w, mixed=True)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), rtol=1e-10, mixed=True)
+    assert info.converged and info.true_rel_residual <= 1e-10
+    r = w.rhs - oracle.matvec(J, host(x))
+    assert np.linalg.norm(r) / np.linalg.norm(w.rhs) <= 1e-10
+    D = np.stack([oracle.matvec(J, e) for e in np.eye(w.n)], axis=1)
+    kappa = np.linalg.cond(D)
+    x64 = np.linalg.solve(D, w.rhs)
+    assert np.linalg.norm(host(x) - x64) <= 1.01 * kappa * 1e-10 * np.linalg.norm(x64)
+    # FP32 operators themselves: within FP32 rounding of the FP64 oracle
+    import torch
+    xx = np.random.default_rng(3).standard_normal(w.n)
+    y32 = host(jac.matvec(dev(xx).float())).astype(np.float64)
+    yo = oracle.matvec(J, xx)
+    assert np.linalg.norm(y32 - yo) / np.linalg.norm(yo) <= 1e-6
+    z32 = host(jac.bjacobi_apply(dev(xx).float())).astype(np.float64)
+    zo = oracle.bj_apply(oracle.bj_setup(J), xx)
+    assert np.linalg.norm(z32 - zo) / np.linalg.norm(zo) <= 1e-6
+    del torch
+    jac.close()
+
+
+# ---------------------------------------------------------------- adjoint
+
+
+def test_grad_matches_oracle_outer_products():
+    for name in ("ragged5x3", "pairs9_2", "band4_r3"):
+        w = workload(name)
+        J = oracle_jac(w)
+        jac = _jac(w, transpose=True)
+        rng = np.random.default_rng(4)
+        lam, x = rng.standard_normal(w.n), rng.standard_normal(w.n)
+        gS, gU, gV = jac.grad(dev(lam), dev(x))
+        rS, rU, rV = oracle.grad(J, lam, x)
+        assert rel_err(host(gS), rS) <= TOL64
+        assert rel_err(host(gU), rU) <= TOL64
+        assert rel_err(host(gV), rV) <= TOL64
+        jac.close()
+
+
+def test_implicit_solve_autograd_vs_oracle_and_fd():
+    import torch
+    from paper_2403_09198_gb300.autograd import ImplicitSolve
+    w = inputs.make_workload(3, 2, N=3, w=1, r_diag=2, r_off=1, seed=21, dt=0.2)
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True)
+    Wd = dev(w.W)
+    params = [dev(a).requires_grad_(True) for a in (w.rhs, w.S, w.U, w.V)]
+
+    def loss_of(b, S, U, V):
+        x = ImplicitSolve.apply(b, S, U, V, jac, 1e-14, 30)
+        return 0.5 * torch.sum((Wd * x) ** 2)
+
+    L = loss_of(*params)
+    L.backward()
+    grads = [host(p.grad) for p in params]
+    ref = oracle.adjoint(J, w.rhs, w.W)
+    for g, r in zip(grads, (ref["gb"], ref["gS"], ref["gU"], ref["gV"])):
+        assert rel_err(g, r) <= 1e-10
+    rng = np.random.default_rng(22)
+    h = 1e-6
+    base = [host(p.detach()) for p in params]
+    with torch.no_grad():
+        for _ in range(64):
+            d = [rng.standard_normal(a.shape) for a in base]
+            d = [di / np.linalg.norm(di) for di in d]
+            tot = np.sqrt(sum(float(np.sum(di * di)) for di in d))
+            d = [di / tot for di in d]
+            gd = sum(float(np.sum(g * di)) for g, di in zip(grads, d))
+            Lp = float(loss_of(*[dev(a + h * di) for a, di in zip(base, d)]))
+            Lm = float(loss_of(*[dev(a - h * di) for a, di in zip(base, d)]))
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(gd - fd) <= 1e-6 * max(abs(fd), 1e-12 * np.sqrt(sum(np.sum(g * g) for g in grads)))
+    jac.close()
+
+
+def test_adjoint_full_size_sampled():
+    """128 x 128, N = 60, seed 4: adjoint GMRES on the transposed operators; the
+    oracle checks J^T lambda = W^2 x on sampled rows and the outer products."""
+    w = inputs.named_workload("grid128_N60_adjoint")
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), rtol=1e-12)
+    assert info.converged
+    xh = host(x)
+    g = w.W * w.W * xh
+    lam, it = jac.gmres(dev(g), rtol=1e-12, trans=True)
+    assert it.converged
+    lh = host(lam)
+    rng = np.random.default_rng(5)
+    rows = rng.choice(w.n, 2000, replace=False)
+    res = oracle.matvec_rows(J, lh, rows, trans=True) - g[rows]
+    assert np.linalg.norm(res) <= 1e-11 * np.linalg.norm(g[rows]) * 10
+    gS, gU, gV = jac.grad(lam, x)
+    rS, rU, rV = oracle.grad(J, lh, xh)
+    for a, b in ((gS, rS), (gU, rU), (gV, rV)):
+        assert rel_err(host(a), b) <= TOL64
+    jac.close()
+
+
+# ---------------------------------------------------------------- dense-BSR baseline
+
+
+@pytest.mark.parametrize("name", ["grid16_N10", "ragged5x3", "pairs9_2", "band4_r3"])
+def test_dense_bsr_baseline(name):
+    w = workload(name)
+    J = oracle_jac(w)
+    jac = _jac(w, dense=True)
+    x = np.random.default_rng(6).standard_normal(w.n)
+    assert rel_err(host(jac.matvec(dev(x))), oracle.matvec(J, x)) <= TOL64
+    jac.bjacobi_setup()
+    assert rel_err(host(jac.bjacobi_apply(dev(x))), oracle.bj_apply(oracle.bj_setup(J), x)) <= TOL64
+    xs, info = jac.gmres(dev(w.rhs), rtol=1e-12)
+    assert info.converged
+    assert rel_err(host(xs), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
+    jac.close()
+
+
+def test_memory_linear_in_N():
+    """Bytes held by a factored handle grow linearly in N, dense ones quadratically."""
+    sizes = {}
+    for N in (10, 20, 40):
+        w = inputs.make_workload(16, 16, N=N, w=2, seed=0)
+        f = _jac(w)
+        d = _jac(w, dense=True)
+        sizes[N] = (f.memory_bytes(), d.memory_bytes())
+        f.close()
+        d.close()
+    bs = np.log([13, 23, 43])                     # block size b = N + 3
+    f_slope = np.polyfit(bs, np.log([sizes[n][0] for n in (10, 20, 40)]), 1)[0]
+    d_slope = np.polyfit(bs, np.log([sizes[n][1] for n in (10, 20, 40)]), 1)[0]
+    assert f_slope < 1.2 and d_slope > 1.7, (f_slope, d_slope)
