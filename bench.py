@@ -129,20 +129,23 @@ def _dist():
     return ws, rank, local
 
 
-def oracle_sample(w, n_ops: int):
-    """Time the FP64 oracle (as it stands) on the host cores: n_ops matvecs and
-    n_ops block-Jacobi applies of the same workload, factors set up untimed."""
+def oracle_sample(w, seconds: float, max_pairs: int = 2000):
+    """Time the FP64 oracle (as it stands) on the host cores: (matvec, block-Jacobi
+    apply) pairs of the same workload until about ``seconds`` have elapsed;
+    the block factors are set up once, untimed."""
     import numpy as np
     import oracle
     J = oracle.Jacobian.from_workload(w)
     F = oracle.bj_setup(J)
     x = np.random.default_rng(0).standard_normal(w.n)
     t0 = time.perf_counter()
-    for _ in range(n_ops):
+    pairs = 0
+    while pairs < max_pairs and (pairs == 0 or time.perf_counter() - t0 < seconds):
         oracle.matvec(J, x)
         oracle.bj_apply(F, x)
+        pairs += 1
     dt = time.perf_counter() - t0
-    return 2 * n_ops / dt, dt, oracle.max_threads()
+    return 2 * pairs / dt, dt, oracle.max_threads(), pairs
 
 
 def run_reference(args):
@@ -373,9 +376,9 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        v, dt, cores = oracle_sample(w, args.cpu_ops)
+        v, dt, cores, pairs = oracle_sample(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_ops} dense-block matvecs + {args.cpu_ops} dense-LU block-Jacobi "
+               "sample": f"{pairs} dense-block matvecs + {pairs} dense-LU block-Jacobi "
                          f"applies of {WORKLOAD} on the host cores ({dt:.1f} s)"}
 
     traffic = _traffic_record()
@@ -424,7 +427,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--ops", type=int, default=1000, help="explicit matvec / apply loop length per step")
-    p.add_argument("--cpu-ops", type=int, default=10)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

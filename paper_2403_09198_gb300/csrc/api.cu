@@ -80,6 +80,34 @@ void transpose_pattern(int b, const std::vector<int> &ptr, const std::vector<int
         }
 }
 
+// Band half-width w if rows p < N = b - kStructNF hold exactly the level band
+// |p - q| <= w followed by the kStructNF flow columns and the last kStructNF
+// rows are dense; -1 if the pattern is not of that family.
+int struct_band(int b, const std::vector<int> &ptr, const std::vector<int> &idx) {
+    const int N = b - kStructNF;
+    if (N < 1) return -1;
+    for (int r = N; r < b; ++r) {
+        if (ptr[r + 1] - ptr[r] != b) return -1;
+        for (int e = ptr[r]; e < ptr[r + 1]; ++e)
+            if (idx[e] != e - ptr[r]) return -1;
+    }
+    for (int w = 0; w <= kStructMaxW; ++w) {
+        bool ok = true;
+        for (int p = 0; p < N && ok; ++p) {
+            const int lo = std::max(0, p - w), hi = std::min(N - 1, p + w);
+            if (ptr[p + 1] - ptr[p] != (hi - lo + 1) + kStructNF) {
+                ok = false;
+                break;
+            }
+            int e = ptr[p];
+            for (int q = lo; q <= hi; ++q, ++e) ok = ok && idx[e] == q;
+            for (int f = 0; f < kStructNF; ++f, ++e) ok = ok && idx[e] == N + f;
+        }
+        if (ok) return w;
+    }
+    return -1;
+}
+
 // Build the plan of one matvec direction (dir 0: y = J x, dir 1: y = J^T x).
 sts_status build_plan(sts_jac_s *h, int dir, bool with_streams) {
     MvPlan &P = h->mv[dir];
@@ -155,42 +183,114 @@ sts_status build_plan(sts_jac_s *h, int dir, bool with_streams) {
         }
     }
     P.n_pslots = (int)pslot_slot.size();
-    // main stream order and row offsets
+    // structured family?  (diagonal kind: band wd; neighbour kind: band 0)
+    const int wd = struct_band(b, kp[0], ki[0]);
+    const int wo = n_slots > 1 ? struct_band(b, kp[1], ki[1]) : 0;
+    P.structured = wd >= 0 && wo == 0 && n_slots <= kStructMaxSlots;
     std::vector<long long> row_off(b + 1, 0);
     std::vector<int> pos_kind, pos_arg;
-    long long maxlen = 0;
-    for (int p = 0; p < b; ++p) {
-        const long long start = (long long)pos_kind.size();
-        for (int s = 0; s < n_slots; ++s) {
-            const int kind = s == 0 ? 0 : 1;
-            const int off = kind ? h->nnz_d : 0;
-            for (int e = kp[kind][p]; e < kp[kind][p + 1]; ++e) {
-                pos_kind.push_back(s);
-                pos_arg.push_back(off + e);
+    std::vector<int> grp(1, 0);
+    std::vector<int> dtask_slot, dpos_kind, dpos_arg;
+    const int Lp = (b + 15) / 16 * 16;      // dot length padded to the largest register chunk
+    P.Lp = Lp;
+    if (P.structured) {
+        const int NF = kStructNF, N = b - NF;
+        std::vector<int> ent[2];
+        for (int k = 0; k < 2; ++k) {
+            ent[k].assign((size_t)b * b, -1);
+            for (int p = 0; p < b; ++p)
+                for (int e = kp[k][p]; e < kp[k][p + 1]; ++e) ent[k][(size_t)p * b + ki[k][e]] = e;
+        }
+        auto push = [&](int kind, int arg) {
+            pos_kind.push_back(kind);
+            pos_arg.push_back(arg);
+        };
+        for (int p = 0; p < N; ++p) {
+            for (int k = 0; k <= 2 * wd; ++k) {
+                const int q = p - wd + k;
+                if (q >= 0 && q < N) push(0, ent[0][(size_t)p * b + q]);
+                else push(kPosZero, 0);
+            }
+            for (int f = 0; f < NF; ++f) push(0, ent[0][(size_t)p * b + N + f]);
+            for (int sl = 1; sl < n_slots; ++sl) {
+                push(sl, h->nnz_d + ent[1][(size_t)p * b + p]);
+                for (int f = 0; f < NF; ++f) push(sl, h->nnz_d + ent[1][(size_t)p * b + N + f]);
+            }
+            for (int k = 0; k < P.n_pslots; ++k) push(-1 - k, p);
+        }
+        for (int f = 0; f < NF; ++f)
+            for (int k = 0; k < P.n_pslots; ++k) push(-1 - k, N + f);
+        // pass-1 tasks: pair dots, then the dense flow rows of every slot
+        for (int k = 0; k < P.n_pslots; ++k) {
+            dtask_slot.push_back(pslot_slot[k]);
+            for (int q = 0; q < Lp; ++q) {
+                dpos_kind.push_back(q < b ? -1 - k : kPosZero);
+                dpos_arg.push_back(q < b ? q : 0);
             }
         }
+        for (int f = 0; f < NF; ++f)
+            for (int sl = 0; sl < n_slots; ++sl) {
+                const int kd = sl == 0 ? 0 : 1;
+                dtask_slot.push_back(sl);
+                for (int q = 0; q < Lp; ++q) {
+                    dpos_kind.push_back(q < b ? sl : kPosZero);
+                    dpos_arg.push_back(q < b ? (kd ? h->nnz_d : 0) + ent[kd][(size_t)(N + f) * b + q] : 0);
+                }
+            }
+        P.s_wd = wd;
+        P.sN = N;
+        P.s_rl = (2 * wd + 1 + NF) + (n_slots - 1) * (1 + NF) + P.n_pslots;
+        P.s_gl = std::max(1, (180 + P.s_rl / 2) / P.s_rl);
+        P.n_lgroups = (N + P.s_gl - 1) / P.s_gl;
+        P.n_groups = P.n_lgroups + 1;
+        P.tile_len = (long long)pos_kind.size();
+        if (P.tile_len != (long long)N * P.s_rl + (long long)NF * P.n_pslots)
+            return set_error(STS_ERR_INVALID_ARG, "internal: structured stream size");
+        for (int g = 1; g <= P.n_lgroups; ++g) grp.push_back(std::min(N, g * P.s_gl));
+        grp.push_back(b);
+    } else {
+        // main stream order and row offsets
+        long long maxlen = 0;
+        for (int p = 0; p < b; ++p) {
+            const long long start = (long long)pos_kind.size();
+            for (int s = 0; s < n_slots; ++s) {
+                const int kind = s == 0 ? 0 : 1;
+                const int off = kind ? h->nnz_d : 0;
+                for (int e = kp[kind][p]; e < kp[kind][p + 1]; ++e) {
+                    pos_kind.push_back(s);
+                    pos_arg.push_back(off + e);
+                }
+            }
+            for (int k = 0; k < P.n_pslots; ++k) {
+                pos_kind.push_back(-1 - k);
+                pos_arg.push_back(p);
+            }
+            row_off[p + 1] = (long long)pos_kind.size();
+            maxlen = std::max(maxlen, row_off[p + 1] - start);
+        }
+        P.tile_len = row_off[b];
+        // row groups: contiguous rows, balanced by stream length
+        const long long target = std::max(maxlen, (P.tile_len + 15) / 16);
+        long long cur = 0;
+        for (int p = 0; p < b; ++p) {
+            const long long len = row_off[p + 1] - row_off[p];
+            if (cur > 0 && cur + len > target) {
+                grp.push_back(p);
+                cur = 0;
+            }
+            cur += len;
+        }
+        grp.push_back(b);
+        P.n_groups = (int)grp.size() - 1;
         for (int k = 0; k < P.n_pslots; ++k) {
-            pos_kind.push_back(-1 - k);
-            pos_arg.push_back(p);
+            dtask_slot.push_back(pslot_slot[k]);
+            for (int q = 0; q < Lp; ++q) {
+                dpos_kind.push_back(q < b ? -1 - k : kPosZero);
+                dpos_arg.push_back(q < b ? q : 0);
+            }
         }
-        row_off[p + 1] = (long long)pos_kind.size();
-        maxlen = std::max(maxlen, row_off[p + 1] - start);
     }
-    P.tile_len = row_off[b];
-    // row groups: contiguous rows, balanced by stream length
-    const long long target = std::max(maxlen, (P.tile_len + 15) / 16);
-    std::vector<int> grp(1, 0);
-    long long cur = 0;
-    for (int p = 0; p < b; ++p) {
-        const long long len = row_off[p + 1] - row_off[p];
-        if (cur > 0 && cur + len > target) {
-            grp.push_back(p);
-            cur = 0;
-        }
-        cur += len;
-    }
-    grp.push_back(b);
-    P.n_groups = (int)grp.size() - 1;
+    P.n_dtasks = (int)dtask_slot.size();
     P.h_grp_rows = grp;
     P.h_row_off = row_off;
     P.h_pslot_slot = pslot_slot;
@@ -208,36 +308,41 @@ sts_status build_plan(sts_jac_s *h, int dir, bool with_streams) {
     STS_TRY(upload(h, &P.row_off, row_off));
     STS_TRY(upload(h, &P.pslot_slot, pslot_slot));
     STS_TRY(upload(h, &P.pslot_local, pslot_local));
+    STS_TRY(upload(h, &P.dtask_slot, dtask_slot));
     STS_TRY(upload(h, &P.pat_ptr, pat_ptr));
     STS_TRY(upload(h, &P.pat_idx, pat_idx));
     STS_TRY(upload(h, &P.pat_src, pat_src));
     if (with_streams) {
         if (b > 0xffff) return set_error(STS_ERR_INVALID_ARG, "block_size above 65535 is not supported");
-        std::vector<unsigned> desc(pos_kind.size());
-        for (int p = 0; p < b; ++p)
-            for (long long q = row_off[p]; q < row_off[p + 1]; ++q) {
-                const int kind = pos_kind[q];
-                unsigned d;
-                if (kind >= 0) {
-                    const int kd = kind == 0 ? 0 : 1;
-                    const int e = pos_arg[q] - (kd ? h->nnz_d : 0);
-                    d = (unsigned)ki[kd][e] | ((unsigned)kind << 16);
-                } else {
-                    d = (unsigned)(-1 - kind) | kDescPair;
+        std::vector<unsigned> desc(P.structured ? 1 : pos_kind.size(), 0u);
+        if (!P.structured) {
+            for (int p = 0; p < b; ++p)
+                for (long long q = row_off[p]; q < row_off[p + 1]; ++q) {
+                    const int kind = pos_kind[q];
+                    unsigned d;
+                    if (kind >= 0) {
+                        const int kd = kind == 0 ? 0 : 1;
+                        const int e = pos_arg[q] - (kd ? h->nnz_d : 0);
+                        d = (unsigned)ki[kd][e] | ((unsigned)kind << 16);
+                    } else {
+                        d = (unsigned)(-1 - kind) | kDescPair;
+                    }
+                    if (q == row_off[p + 1] - 1) d |= kDescEnd;
+                    desc[q] = d;
                 }
-                if (q == row_off[p + 1] - 1) d |= kDescEnd;
-                desc[q] = d;
-            }
-        // a row with no stream positions still has to be written (as zero)
-        for (int p = 0; p < b; ++p)
-            if (row_off[p + 1] == row_off[p])
-                return set_error(STS_ERR_INVALID_ARG, "row %d of the Jacobian blocks is empty in every slot; "
-                                 "add an explicit zero to the pattern", p);
+            // a row with no stream positions would never be written
+            for (int p = 0; p < b; ++p)
+                if (row_off[p + 1] == row_off[p])
+                    return set_error(STS_ERR_INVALID_ARG, "row %d of the Jacobian blocks is empty in every slot; "
+                                     "add an explicit zero to the pattern", p);
+        }
         STS_TRY(upload(h, &P.desc, desc));
         STS_TRY(upload(h, &P.pos_kind, pos_kind));
         STS_TRY(upload(h, &P.pos_arg, pos_arg));
+        STS_TRY(upload(h, &P.dpos_kind, dpos_kind));
+        STS_TRY(upload(h, &P.dpos_arg, dpos_arg));
         const size_t nm = (size_t)nt * P.tile_len * kTile;
-        const size_t nd = (size_t)nt * P.n_pslots * b * kTile;
+        const size_t nd = (size_t)nt * P.n_dtasks * Lp * kTile;
         STS_TRY(dalloc(h, &P.main64, nm));
         STS_TRY(dalloc(h, &P.dotv64, nd));
         if (h->dtype == STS_MIXED) {
@@ -281,7 +386,7 @@ sts_status build_grad_tables(sts_jac_s *h) {
                 for (int lane = 0; lane < kTile; ++lane) {
                     const int k = hblk[((size_t)t * P.n_slots + s) * kTile + lane];
                     if (k < 0) continue;
-                    dst[h->pbase[k] + local] = (int)(((size_t)t * P.n_pslots + ps) * kTile + lane);
+                    dst[h->pbase[k] + local] = (int)(((size_t)t * P.n_dtasks + ps) * kTile + lane);
                 }
             }
     }
@@ -403,7 +508,7 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
         const size_t n = (size_t)b * h->ncp;
         if ((st = dalloc(h, &h->vin, n)) != STS_OK) break;
         if ((st = dalloc(h, &h->vout, n)) != STS_OK) break;
-        const int nps = std::max(h->mv[0].n_pslots, h->mv[1].n_pslots);
+        const int nps = std::max(h->mv[0].n_dtasks, h->mv[1].n_dtasks);
         if ((st = dalloc(h, &h->c64, (size_t)h->n_tiles * nps * kTile + 1)) != STS_OK) break;
         if (h->dtype == STS_MIXED) {
             if ((st = dalloc(h, &h->vin32, n)) != STS_OK) break;

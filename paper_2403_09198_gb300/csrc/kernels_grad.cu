@@ -50,7 +50,7 @@ __global__ void k_grad_UV(double *gU, double *gV, const double *lam, const doubl
 sts_status grad(sts_jac_s *h, const double *lam, const double *x, double *gS, double *gU, double *gV) {
     if (!h->g_c) {
         // internal copies of lambda and x plus the transposed pair dots
-        STS_TRY(dalloc(h, &h->g_c, (size_t)h->n_tiles * h->mv[1].n_pslots * kTile + 1));
+        STS_TRY(dalloc(h, &h->g_c, (size_t)h->n_tiles * h->mv[1].n_dtasks * kTile + 1));
     }
     double *li = h->vin, *xi = h->vout;
     STS_TRY(to_internal64(h, lam, li));

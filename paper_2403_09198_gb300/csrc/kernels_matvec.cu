@@ -12,6 +12,8 @@
 // same kernels on the transposed plan (S^T patterns, roles of u and v swapped).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "sts_internal.h"
 
 namespace sts {
@@ -20,72 +22,85 @@ namespace {
 template <typename T>
 struct MvArgs {
     const T *main;          // [n_tiles][tile_len][32]
-    const T *dotv;          // [n_tiles][n_pslots][b][32]
+    const T *dotv;          // [n_tiles][n_dtasks][Lp][32]
     const T *x;             // [b][ncp]
     T *y;                   // [b][ncp]
-    T *c;                   // [n_tiles][n_pslots][32]
+    T *c;                   // [n_tiles][n_dtasks][32]
     const int *nbr;         // [n_tiles][n_slots][32]
     const unsigned *slot_mask;
     const int *grp_rows;
     const long long *row_off;
-    const int *pslot_slot;
+    const int *dtask_slot;  // [n_dtasks]
     const int *pat_ptr;     // [2][b+1]
     const int *pat_idx;
-    const unsigned *desc;   // [tile_len] program of the main pass
+    const unsigned *desc;   // [tile_len] program of the generic main pass
     long long tile_len;
-    int n_tiles, n_slots, n_pslots, n_groups, b, ncp, nnz_d;
+    int n_tiles, n_slots, n_pslots, n_dtasks, Lp, n_groups, b, ncp, nnz_d;
+    int sN, s_rl, s_gl, n_lgroups, wd, structured;   // structured layout (see MvPlan)
 };
 
-// Chunk of stream positions held in registers; the next chunk is loaded while
-// the current one is consumed, so every warp keeps CH coalesced requests in
-// flight independently of its FMA dependency chain.
+// Chunk of stream positions held in registers.
 template <typename T> struct Chunk { static constexpr int CH = 8; };
 template <> struct Chunk<float> { static constexpr int CH = 16; };
 
-// Pass 1: one warp per (tile, pair slot); lane = cell; serial dot over q.
+// Pass 1: one warp per (tile, dot task); lane = cell.  A dot task is one
+// length-b dot product  c = d . x_j  with j the neighbour of the task's slot:
+// the pair dots v . x_j of every rank-one pair and, for the paper's pattern
+// family, the dense flow rows of S.  Two register buffers alternate so the
+// loads of the next chunk are in flight while the current one is multiplied;
+// the stream is padded to Lp (a multiple of the chunk) with zero coefficients.
 template <typename T>
-__global__ void __launch_bounds__(128) k_pair_dots(MvArgs<T> a) {
+__global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
     constexpr int CH = Chunk<T>::CH;
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wid >= (long long)a.n_tiles * a.n_pslots) return;
-    const int t = (int)(wid / a.n_pslots), k = (int)(wid % a.n_pslots);
-    const int s = a.pslot_slot[k];
+    if (wid >= (long long)a.n_tiles * a.n_dtasks) return;
+    const int t = (int)(wid / a.n_dtasks), k = (int)(wid % a.n_dtasks);
+    const int s = a.dtask_slot[k];
     T acc = T(0);
     if ((a.slot_mask[t] >> s) & 1u) {
         const int j = a.nbr[((size_t)t * a.n_slots + s) * kTile + lane];
-        const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_pslots + k) * a.b * kTile + lane;
-        const T *__restrict__ xj = a.x + (j < 0 ? 0 : j);
-        const bool on = j >= 0;
-        const int L = a.b;
-        T cur[CH], nxt[CH];
+        // an absent neighbour reads the lane's own cell: its coefficients are zero
+        const T *__restrict__ xj = a.x + (j >= 0 ? j : t * kTile + lane);
+        const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_dtasks + k) * a.Lp * kTile + lane;
+        const int bm1 = a.b - 1;
+        const size_t ncp = a.ncp;
+        T va[CH], xa[CH], vb[CH], xb[CH];
 #pragma unroll
-        for (int i = 0; i < CH; ++i) cur[i] = i < L ? __ldg(dv + (size_t)i * kTile) : T(0);
-        for (int base = 0; base < L; base += CH) {
+        for (int i = 0; i < CH; ++i) {
+            va[i] = __ldg(dv + (size_t)i * kTile);
+            xa[i] = __ldg(xj + (size_t)min(i, bm1) * ncp);
+        }
+        for (int base = 0; base < a.Lp; base += 2 * CH) {
+            if (base + CH < a.Lp) {
 #pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int pp = base + CH + i;
-                nxt[i] = pp < L ? __ldg(dv + (size_t)pp * kTile) : T(0);
-            }
-#pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int q = base + i;
-                if (q < L) {
-                    const T xv = on ? __ldg(xj + (size_t)q * a.ncp) : T(0);
-                    acc = fma(cur[i], xv, acc);
+                for (int i = 0; i < CH; ++i) {
+                    vb[i] = __ldg(dv + (size_t)(base + CH + i) * kTile);
+                    xb[i] = __ldg(xj + (size_t)min(base + CH + i, bm1) * ncp);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < CH; ++i) cur[i] = nxt[i];
+            for (int i = 0; i < CH; ++i) acc = fma(va[i], xa[i], acc);
+            if (base + CH >= a.Lp) break;
+            if (base + 2 * CH < a.Lp) {
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    va[i] = __ldg(dv + (size_t)(base + 2 * CH + i) * kTile);
+                    xa[i] = __ldg(xj + (size_t)min(base + 2 * CH + i, bm1) * ncp);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CH; ++i) acc = fma(vb[i], xb[i], acc);
         }
     }
-    a.c[((size_t)t * a.n_pslots + k) * kTile + lane] = acc;
+    a.c[((size_t)t * a.n_dtasks + k) * kTile + lane] = acc;
 }
 
-// Pass 2: one warp per (tile, row group); lane = cell.  The group's stream
-// positions are consumed in order under a flat program (one descriptor per
-// position: column and block slot of an S entry, or the pair slot of a pair
-// term, plus an end-of-row flag); each row is accumulated serially.
+// Pass 2, generic patterns: one warp per (tile, row group); lane = cell.  The
+// group's stream positions are consumed in order under a flat program (one
+// descriptor per position: column and block slot of an S entry, or the pair
+// slot of a pair term, plus an end-of-row flag); each row is accumulated
+// serially.  Stream values are double-buffered in registers one chunk ahead.
 template <typename T>
 __global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
     constexpr int CH = Chunk<T>::CH;
@@ -102,7 +117,7 @@ __global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
     const T *__restrict__ sv = a.main + ((size_t)t * a.tile_len + q0) * kTile + lane;
     const unsigned *__restrict__ dd = a.desc + q0;
     const T *__restrict__ xp = a.x;
-    const T *__restrict__ cc = a.c + (size_t)t * a.n_pslots * kTile + lane;
+    const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
     T *__restrict__ yp = a.y + (size_t)p0 * a.ncp + (size_t)t * kTile + lane;
     T cur[CH], nxt[CH];
 #pragma unroll
@@ -139,9 +154,84 @@ __global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
     }
 }
 
-// Repack the public values into the main stream of one direction.
+// Pass 2, the paper's pattern family (arrow + level band, see MvPlan): column
+// indices are arithmetic, so no program is read.  Warps of a tile are groups
+// of s_gl level rows, plus one warp for the dense flow rows, whose products
+// with x came out of pass 1:
+//   level row p: diagonal-slot band q = p-WD..p+WD and the NF flow columns,
+//                every neighbour slot's entry q = p and its flow columns, then
+//                the pair terms u_k[p] c_k.  The flow-column x values of every
+//                slot stay in registers for the whole group.
+//   flow row N+f: sum over slots of the pass-1 flow dots, then the pair terms.
+template <typename T, int WD>
+__global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
+    constexpr int NF = kStructNF;
+    constexpr int NS = kStructMaxSlots;
+    constexpr int RD = 2 * WD + 1 + NF;          // diagonal-slot entries of a level row
+    const int lane = threadIdx.x & 31;
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= (long long)a.n_tiles * a.n_groups) return;
+    const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
+    const int ns = a.n_slots, nps = a.n_pslots, N = a.sN;
+    const size_t ncp = a.ncp;
+    const unsigned mask = a.slot_mask[t];
+    const size_t cell = (size_t)t * kTile + lane;
+    const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
+    const T *__restrict__ tile_stream = a.main + (size_t)t * a.tile_len * kTile + lane;
+    if (g == a.n_lgroups) {
+        const T *__restrict__ su = tile_stream + (size_t)N * a.s_rl * kTile;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            T acc = T(0);
+            for (int s = 0; s < ns; ++s) acc += __ldg(cc + (size_t)(nps + f * ns + s) * kTile);
+            for (int k = 0; k < nps; ++k)
+                acc = fma(__ldg(su + (size_t)(f * nps + k) * kTile), __ldg(cc + (size_t)k * kTile), acc);
+            a.y[(size_t)(N + f) * ncp + cell] = acc;
+        }
+        return;
+    }
+    const T *xs[NS];
+    T xf[NS][NF];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int j = s < ns ? a.nbr[((size_t)t * ns + s) * kTile + lane] : -1;
+        // an absent neighbour reads the lane's own cell: its coefficients are zero
+        xs[s] = a.x + (j >= 0 ? (size_t)j : cell);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) xf[s][f] = s < ns ? __ldg(xs[s] + (size_t)(N + f) * ncp) : T(0);
+    }
+    const int p0 = g * a.s_gl, p1 = min(N, p0 + a.s_gl);
+    for (int p = p0; p < p1; ++p) {
+        const T *__restrict__ sr = tile_stream + (size_t)p * a.s_rl * kTile;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k <= 2 * WD; ++k) {
+            const int q = min(max(p - WD + k, 0), N - 1);    // clipped band entries carry zeros
+            acc = fma(__ldg(sr + (size_t)k * kTile), __ldg(xs[0] + (size_t)q * ncp), acc);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc = fma(__ldg(sr + (size_t)(2 * WD + 1 + f) * kTile), xf[0][f], acc);
+#pragma unroll
+        for (int s = 1; s < NS; ++s) {
+            if (s < ns && ((mask >> s) & 1u)) {
+                const T *__restrict__ so = sr + (size_t)(RD + (s - 1) * (1 + NF)) * kTile;
+                acc = fma(__ldg(so), __ldg(xs[s] + (size_t)p * ncp), acc);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) acc = fma(__ldg(so + (size_t)(1 + f) * kTile), xf[s][f], acc);
+            }
+        }
+        const T *__restrict__ su = sr + (size_t)(RD + (ns - 1) * (1 + NF)) * kTile;
+        for (int k = 0; k < nps; ++k) acc = fma(__ldg(su + (size_t)k * kTile), __ldg(cc + (size_t)k * kTile), acc);
+        a.y[(size_t)p * ncp + cell] = acc;
+    }
+}
+
+// Repack the public values into one stream of one direction.  Each stream
+// position (per tile and lane) is an S entry of a block slot, an entry of a
+// pair vector (the axpy vectors in the main stream, the dot vectors in the
+// pass-1 stream), or a zero.
 template <typename T>
-__global__ void k_repack_main(T *out, const double *S, const double *AX, const int *blk,
+__global__ void k_repack(T *out, const double *S, const double *AX, const int *blk,
                               const long long *soff, const int *pbase, const int *pos_kind,
                               const int *pos_arg, const int *pat_src, const int *pslot_slot,
                               const int *pslot_local, long long tile_len, int n_tiles, int n_slots,
@@ -155,7 +245,9 @@ __global__ void k_repack_main(T *out, const double *S, const double *AX, const i
         const int t = (int)(r / tile_len);
         const int kind = pos_kind[pos], arg = pos_arg[pos];
         double v = 0.0;
-        if (kind >= 0) {
+        if (kind == kPosZero) {
+            v = 0.0;
+        } else if (kind >= 0) {
             const int k = blk[((size_t)t * n_slots + kind) * kTile + lane];
             if (k >= 0) v = S[soff[k] + pat_src[arg]];
         } else {
@@ -163,26 +255,6 @@ __global__ void k_repack_main(T *out, const double *S, const double *AX, const i
             const int k = blk[((size_t)t * n_slots + pslot_slot[ps]) * kTile + lane];
             if (k >= 0) v = AX[(size_t)(pbase[k] + pslot_local[ps]) * b + arg];
         }
-        out[i] = (T)v;
-    }
-}
-
-template <typename T>
-__global__ void k_repack_dots(T *out, const double *DV, const int *blk, const int *pbase,
-                              const int *pslot_slot, const int *pslot_local, int n_tiles,
-                              int n_slots, int n_pslots, int b) {
-    const long long total = (long long)n_tiles * n_pslots * b * kTile;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int lane = (int)(i % kTile);
-        long long r = i / kTile;
-        const int q = (int)(r % b);
-        r /= b;
-        const int ps = (int)(r % n_pslots);
-        const int t = (int)(r / n_pslots);
-        const int k = blk[((size_t)t * n_slots + pslot_slot[ps]) * kTile + lane];
-        double v = 0.0;
-        if (k >= 0) v = DV[(size_t)(pbase[k] + pslot_local[ps]) * b + q];
         out[i] = (T)v;
     }
 }
@@ -259,7 +331,7 @@ MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T
     a.slot_mask = P.slot_mask;
     a.grp_rows = P.grp_rows;
     a.row_off = P.row_off;
-    a.pslot_slot = P.pslot_slot;
+    a.dtask_slot = P.dtask_slot;
     a.pat_ptr = P.pat_ptr;
     a.pat_idx = P.pat_idx;
     a.desc = P.desc;
@@ -267,23 +339,46 @@ MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T
     a.n_tiles = h->n_tiles;
     a.n_slots = P.n_slots;
     a.n_pslots = P.n_pslots;
+    a.n_dtasks = P.n_dtasks;
+    a.Lp = P.Lp;
     a.n_groups = P.n_groups;
     a.b = h->b;
     a.ncp = h->ncp;
     a.nnz_d = h->nnz_d;
+    a.sN = P.sN;
+    a.s_rl = P.s_rl;
+    a.s_gl = P.s_gl;
+    a.n_lgroups = P.n_lgroups;
+    a.wd = P.s_wd;
+    a.structured = P.structured ? 1 : 0;
     return a;
 }
 
 template <typename T>
+sts_status dots_launch(sts_jac_s *h, const MvArgs<T> &a) {
+    if (a.n_dtasks == 0) return STS_OK;
+    const long long warps = (long long)a.n_tiles * a.n_dtasks;
+    k_dots<T><<<(unsigned)((warps + 3) / 4), 128, 0, h->stream>>>(a);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
+template <typename T>
 sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
-    const int wpb = 4;
-    if (a.n_pslots > 0) {
-        const long long warps = (long long)a.n_tiles * a.n_pslots;
-        k_pair_dots<T><<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(a);
-        STS_LAUNCHED();
-    }
+    STS_TRY(dots_launch<T>(h, a));
     const long long warps = (long long)a.n_tiles * a.n_groups;
-    k_mv_main<T><<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, h->stream>>>(a);
+    const unsigned grid = (unsigned)((warps + 3) / 4);
+    if (a.structured) {
+        switch (a.wd) {
+            case 0: k_mv_struct<T, 0><<<grid, 128, 0, h->stream>>>(a); break;
+            case 1: k_mv_struct<T, 1><<<grid, 128, 0, h->stream>>>(a); break;
+            case 2: k_mv_struct<T, 2><<<grid, 128, 0, h->stream>>>(a); break;
+            case 3: k_mv_struct<T, 3><<<grid, 128, 0, h->stream>>>(a); break;
+            default: k_mv_struct<T, 4><<<grid, 128, 0, h->stream>>>(a); break;
+        }
+    } else {
+        k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);
+    }
     STS_LAUNCHED();
     return STS_OK;
 }
@@ -292,34 +387,20 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
 
 sts_status mv_repack(sts_jac_s *h, int dir, const double *S, const double *U, const double *V) {
     MvPlan &P = h->mv[dir];
-    const double *AX = dir == 0 ? U : V;   // axpy vectors
-    const double *DV = dir == 0 ? V : U;   // dot vectors
+    const double *AX = dir == 0 ? U : V;   // axpy vectors (main stream)
+    const double *DV = dir == 0 ? V : U;   // dot vectors (pass-1 stream)
     const long long nm = (long long)h->n_tiles * P.tile_len * kTile;
-    const long long nd = (long long)h->n_tiles * P.n_pslots * h->b * kTile;
-    if (P.main64) {
-        k_repack_main<double><<<grid_for(nm, 256), 256, 0, h->stream>>>(
-            P.main64, S, AX, P.blk, h->d_soff, h->d_pbase, P.pos_kind, P.pos_arg, P.pat_src,
-            P.pslot_slot, P.pslot_local, P.tile_len, h->n_tiles, P.n_slots, h->b);
-        STS_LAUNCHED();
-    }
-    if (P.main32) {
-        k_repack_main<float><<<grid_for(nm, 256), 256, 0, h->stream>>>(
-            P.main32, S, AX, P.blk, h->d_soff, h->d_pbase, P.pos_kind, P.pos_arg, P.pat_src,
-            P.pslot_slot, P.pslot_local, P.tile_len, h->n_tiles, P.n_slots, h->b);
-        STS_LAUNCHED();
-    }
-    if (nd > 0 && P.dotv64) {
-        k_repack_dots<double><<<grid_for(nd, 256), 256, 0, h->stream>>>(
-            P.dotv64, DV, P.blk, h->d_pbase, P.pslot_slot, P.pslot_local, h->n_tiles, P.n_slots,
-            P.n_pslots, h->b);
-        STS_LAUNCHED();
-    }
-    if (nd > 0 && P.dotv32) {
-        k_repack_dots<float><<<grid_for(nd, 256), 256, 0, h->stream>>>(
-            P.dotv32, DV, P.blk, h->d_pbase, P.pslot_slot, P.pslot_local, h->n_tiles, P.n_slots,
-            P.n_pslots, h->b);
-        STS_LAUNCHED();
-    }
+    const long long nd = (long long)h->n_tiles * P.n_dtasks * P.Lp * kTile;
+    auto rp = [&](auto *out, const double *vec, const int *pk, const int *pa, long long len, long long total) {
+        using T = std::remove_pointer_t<decltype(out)>;
+        k_repack<T><<<grid_for(total, 256), 256, 0, h->stream>>>(out, S, vec, P.blk, h->d_soff, h->d_pbase, pk, pa,
+                                                                 P.pat_src, P.pslot_slot, P.pslot_local, len,
+                                                                 h->n_tiles, P.n_slots, h->b);
+    };
+    if (P.main64) { rp(P.main64, AX, P.pos_kind, P.pos_arg, P.tile_len, nm); STS_LAUNCHED(); }
+    if (P.main32) { rp(P.main32, AX, P.pos_kind, P.pos_arg, P.tile_len, nm); STS_LAUNCHED(); }
+    if (nd > 0 && P.dotv64) { rp(P.dotv64, DV, P.dpos_kind, P.dpos_arg, (long long)P.n_dtasks * P.Lp, nd); STS_LAUNCHED(); }
+    if (nd > 0 && P.dotv32) { rp(P.dotv32, DV, P.dpos_kind, P.dpos_arg, (long long)P.n_dtasks * P.Lp, nd); STS_LAUNCHED(); }
     return STS_OK;
 }
 
@@ -330,12 +411,7 @@ sts_status mv_apply64(sts_jac_s *h, int dir, const double *x, double *y, double 
 
 sts_status mv_dots64(sts_jac_s *h, int dir, const double *x, double *c) {
     const MvPlan &P = h->mv[dir];
-    MvArgs<double> a = make_args<double>(h, dir, P.main64, P.dotv64, x, nullptr, c);
-    if (a.n_pslots == 0) return STS_OK;
-    const long long warps = (long long)a.n_tiles * a.n_pslots;
-    k_pair_dots<double><<<(unsigned)((warps + 3) / 4), 128, 0, h->stream>>>(a);
-    STS_LAUNCHED();
-    return STS_OK;
+    return dots_launch<double>(h, make_args<double>(h, dir, P.main64, P.dotv64, x, nullptr, c));
 }
 
 sts_status mv_apply32(sts_jac_s *h, int dir, const float *x, float *y, float *c) {

@@ -203,54 +203,80 @@ struct ApplyArgs {
     int len, b, r, ncp, trans;
 };
 
-template <typename T> struct ApChunk { static constexpr int CH = 8; };
-template <> struct ApChunk<float> { static constexpr int CH = 16; };
+constexpr int kApStage = 32;    // stream positions per shared-memory stage
+constexpr int kApStages = 3;    // stages in flight (two ahead of the one consumed)
 
-// One warp per 32 cells, one lane per cell; the working vector lives in
-// shared memory [q][lane].  The triangular sweeps run a flat program (one
-// descriptor per stream position) while the stream is double-buffered in
-// registers, so each lane has the next chunk's loads in flight.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// One warp per 32 cells, one lane per cell.  The tile's apply stream is
+// copied into a ring of shared-memory stages with cp.async two stages ahead of
+// its use; the working vector lives in shared memory [q][lane]; the triangular
+// sweeps run a flat program (one descriptor per stream position).
 template <typename T, int RMAX>
 __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
-    constexpr int CH = ApChunk<T>::CH;
-    extern __shared__ unsigned char smem_raw[];
-    T *w = reinterpret_cast<T *>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
+    T *w = stg + kApStages * kApStage * kTile;                  // [b][32]
+    constexpr int PIECES = kTile * (int)sizeof(T) / 16;         // 16-byte pieces per position
+    constexpr int PER_ITER = kTile / PIECES;                    // positions per warp-wide copy
     const int lane = threadIdx.x;
-    const int cell = blockIdx.x * kTile + lane;
+    const int tile = blockIdx.x;
+    const int cell = tile * kTile + lane;
     const size_t P = a.ncp;
+    const int L = a.len;
+    const int nchunks = (L + kApStage - 1) / kApStage;
+    const T *__restrict__ stream = a.st + (size_t)tile * kTile;
+    auto issue = [&](int c) {
+        T *dst0 = stg + (c % kApStages) * kApStage * kTile;
+        const int piece = lane % PIECES;
+#pragma unroll
+        for (int it = 0; it < kApStage / PER_ITER; ++it) {
+            const int pos = it * PER_ITER + lane / PIECES;
+            const int gp = c * kApStage + pos;
+            if (gp < L)
+                cp_async16(dst0 + pos * kTile + piece * (16 / (int)sizeof(T)),
+                           stream + (size_t)gp * P + piece * (16 / (int)sizeof(T)));
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int c = 0; c < kApStages - 1; ++c) {
+        if (c < nchunks) issue(c);
+        else cp_async_commit();
+    }
     const T *__restrict__ x = a.x;
     for (int i = 0; i < a.b; ++i) w[i * kTile + lane] = __ldg(x + i * P + cell);
-    const T *__restrict__ st = a.st + cell;
     const unsigned *__restrict__ dd = a.desc;
-    const int L = a.len;
-    T cur[CH], nxt[CH];
-#pragma unroll
-    for (int i = 0; i < CH; ++i) cur[i] = i < L ? __ldg(st + (size_t)i * P) : T(0);
     T acc = T(0);
-    for (int base = 0; base < L; base += CH) {
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int pp = base + CH + i;
-            nxt[i] = pp < L ? __ldg(st + (size_t)pp * P) : T(0);
-        }
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int pp = base + i;
-            if (pp < L) {
-                const unsigned d = __ldg(dd + pp);
-                const int row = (d >> 12) & 0xfffu, col = d & 0xfffu;
-                if (d & kApScale) {
-                    acc = cur[i] * w[row * kTile + lane];
-                } else {
-                    if (d & kApBegin) acc = w[row * kTile + lane];
-                    acc = fma(-cur[i], w[col * kTile + lane], acc);
-                }
-                if (d & kApEnd) w[row * kTile + lane] = acc;
+    for (int c = 0; c < nchunks; ++c) {
+        cp_async_wait<kApStages - 2>();
+        __syncwarp();
+        if (c + kApStages - 1 < nchunks) issue(c + kApStages - 1);
+        else cp_async_commit();
+        const T *cur = stg + (c % kApStages) * kApStage * kTile + lane;
+        const unsigned *dc = dd + c * kApStage;
+        const int n_in = min(kApStage, L - c * kApStage);
+#pragma unroll 8
+        for (int i = 0; i < n_in; ++i) {
+            const unsigned d = __ldg(dc + i);
+            const T v = cur[i * kTile];
+            const int row = (d >> 12) & 0xfffu, col = d & 0xfffu;
+            if (d & kApScale) {
+                acc = v * w[row * kTile + lane];
+            } else {
+                if (d & kApBegin) acc = w[row * kTile + lane];
+                acc = fma(-v, w[col * kTile + lane], acc);
             }
+            if (d & kApEnd) w[row * kTile + lane] = acc;
         }
-#pragma unroll
-        for (int i = 0; i < CH; ++i) cur[i] = nxt[i];
     }
+    cp_async_wait<0>();
     // t = dv^T x0, z = C^-1 t (FP64), x = x0 - W z
     T t[RMAX];
 #pragma unroll
@@ -559,7 +585,7 @@ static sts_status smw_apply_t(sts_jac_s *h, int dir, const T *st, const T *dv, c
     ApplyArgs<T> a;
     a.st = st; a.desc = M.ap_desc[dir]; a.dv = dv; a.W = W; a.Cinv = M.Cinv; a.x = x; a.y = z;
     a.len = M.n_fwd[dir] + M.n_bwd[dir] + h->b; a.b = h->b; a.r = h->r_diag; a.ncp = h->ncp; a.trans = dir;
-    const size_t smem = (size_t)h->b * kTile * sizeof(T);
+    const size_t smem = ((size_t)kApStages * kApStage + h->b) * kTile * sizeof(T);
     auto kern = a.r <= 2 ? k_smw_apply<T, 2> : a.r <= 4 ? k_smw_apply<T, 4> : k_smw_apply<T, kMaxPairsDiag>;
     if (smem > 48 * 1024)
         STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

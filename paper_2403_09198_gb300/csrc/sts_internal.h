@@ -34,6 +34,15 @@ constexpr int kMaxPairsDiag = 16;  // rank-one pairs per diagonal block handled 
 //   kDescPair  the position is a pair term u_k[p] * c_k
 //   kDescEnd   the row is complete after this position
 constexpr unsigned kDescPair = 1u << 29;
+constexpr int kPosZero = -2147483647 - 1;     // repack code of a zero (padding) stream position
+
+// Structured pattern family (the paper's StS blocks): the last kStructNF rows
+// of a block are dense "flow" rows; a level row p < N = b - kStructNF holds the
+// level band |p-q| <= w (w = WD for diagonal blocks, 0 for neighbour blocks)
+// and the kStructNF flow columns.  Both S and S^T of such blocks have it.
+constexpr int kStructNF = 3;
+constexpr int kStructMaxW = 4;
+constexpr int kStructMaxSlots = 5;
 constexpr unsigned kDescEnd = 1u << 31;
 
 // SMW apply program descriptor (one per stream position):
@@ -90,6 +99,7 @@ struct DevBuf {
 // T: S in transposed-pattern order, dot-vector U, axpy-vector V, dot input x_row.
 struct MvPlan {
     int n_slots = 0, n_pslots = 0, n_groups = 0;
+    int n_dtasks = 0, Lp = 0;                // pass-1 dot tasks per tile, padded dot length
     long long tile_len = 0;                  // main-stream elements per lane per tile
     std::vector<int> h_grp_rows;             // [n_groups+1]
     std::vector<long long> h_row_off;        // [b+1] start of row p in the tile stream
@@ -106,6 +116,8 @@ struct MvPlan {
     int *pat_ptr = nullptr;                  // [2][b+1] pattern rows (kind 0 diag, 1 off), this direction
     int *pat_idx = nullptr;                  // [nnz_d + nnz_o] column indices (kind 1 after kind 0)
     int *pat_src = nullptr;                  // [nnz_d + nnz_o] public entry index of each pattern entry
+    int *dtask_slot = nullptr;               // [n_dtasks]: block slot whose x a dot task reads
+    int *dpos_kind = nullptr, *dpos_arg = nullptr;   // [n_dtasks*Lp]: pass-1 stream positions
     int *pos_kind = nullptr;                 // [tile_len]: 0..n_slots-1 = S of that slot, -1-k = pair slot k
     int *pos_arg = nullptr;                  // [tile_len]: pattern entry (S) or row p (pair)
     unsigned *desc = nullptr;                // [tile_len]: main-pass program (see kDescPair)
@@ -113,6 +125,15 @@ struct MvPlan {
     float *main32 = nullptr;
     double *dotv64 = nullptr;
     float *dotv32 = nullptr;
+    // Dot tasks: the n_pslots pair dots, then (structured layout only) the
+    // dense flow rows of S, task n_pslots + f*n_slots + s for flow row N+f of
+    // slot s.  Structured main stream, per tile: level rows p < sN (s_rl values
+    // each: diagonal band 2*wd+1 (zero-padded where clipped) + NF flow, then per
+    // neighbour slot 1 + NF, then the pair terms), then per flow row the
+    // n_pslots pair terms.  Warps: n_lgroups groups of s_gl level rows, then one
+    // for the flow rows.
+    bool structured = false;
+    int s_wd = 0, sN = 0, s_rl = 0, s_gl = 0, n_lgroups = 0;
 };
 
 // SMW block-Jacobi data (factored representation).

@@ -149,6 +149,27 @@ def off_pattern(N: int):
     return np.asarray(indptr, dtype=np.int32), np.asarray(cols, dtype=np.int32)
 
 
+def random_patterns(b: int, density: float, seed: int):
+    """Two random b x b CSR patterns (diagonal-block one with every diagonal
+    entry, neighbour one arbitrary but with every row non-empty), for exercising
+    patterns outside the paper's family."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for with_diag in (True, False):
+        indptr = [0]
+        cols: list[int] = []
+        for p in range(b):
+            row = set(np.flatnonzero(rng.random(b) < density).tolist())
+            if with_diag:
+                row.add(p)
+            if not row:
+                row.add(int(rng.integers(b)))
+            cols.extend(sorted(row))
+            indptr.append(len(cols))
+        out.append((np.asarray(indptr, dtype=np.int32), np.asarray(cols, dtype=np.int32)))
+    return out
+
+
 def pair_indptr_for(block_indptr, block_indices, r_diag: int, r_off: int) -> np.ndarray:
     """BR1-BSR ``pair_indptr``: r_diag pairs per diagonal block, r_off per other block."""
     block_indptr = np.asarray(block_indptr, dtype=np.int64)
@@ -170,8 +191,9 @@ def _standard_normal(rng: np.random.Generator, n: int, chunk: int = 1 << 24) -> 
 
 def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
                   r_diag: int = 2, r_off: int = 1, seed: int = 0, dt: float = 1e-3,
-                  same_pattern: bool = False) -> Workload:
-    """Draw one workload; see the module docstring for shapes and distributions."""
+                  same_pattern: bool = False, random_density: float = 0.0) -> Workload:
+    """Draw one workload; see the module docstring for shapes and distributions.
+    ``random_density > 0`` replaces both patterns by random ones of that density."""
     Ly = Lx if Ly is None else Ly
     b = N + 3
     block_indptr, block_indices = mesh_adjacency(Lx, Ly)
@@ -180,6 +202,8 @@ def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
         o_indptr, o_indices = d_indptr.copy(), d_indices.copy()
     else:
         o_indptr, o_indices = off_pattern(N)
+    if random_density > 0:
+        (d_indptr, d_indices), (o_indptr, o_indices) = random_patterns(b, random_density, seed + 1000)
     nc = Lx * Ly
     nnzb = block_indices.shape[0]
     rows = np.repeat(np.arange(nc), np.diff(block_indptr))

@@ -9,8 +9,10 @@ TOL64 = 1e-12
 
 # Small workloads the oracle finishes in seconds; together they cover several
 # tiles and ragged tails, one cell, 1 x L strips, N = 1, no pairs, the paper's
-# physical pair counts (9 per diagonal block, 2 per neighbour block), a shared
-# pattern, and the band +-4 / 3-pair family of the N = 200 workload.
+# physical pair counts (9 per diagonal block, 2 per neighbour block), the
+# band +-4 / 3-pair family of the N = 200 workload, and two patterns outside the
+# paper's family (a shared pattern, random patterns) that take the generic
+# table-driven kernels.
 SMALL = {
     "grid16_N10": dict(Lx=16, N=10, w=2, r_diag=2, r_off=1, seed=0),
     "ragged5x3": dict(Lx=5, Ly=3, N=4, w=1, r_diag=2, r_off=1, seed=1),
@@ -21,6 +23,7 @@ SMALL = {
     "pairs9_2": dict(Lx=6, Ly=5, N=8, w=2, r_diag=9, r_off=2, seed=6),
     "same_pattern": dict(Lx=8, Ly=4, N=6, w=2, r_diag=2, r_off=1, seed=7, same_pattern=True),
     "band4_r3": dict(Lx=33, Ly=2, N=12, w=4, r_diag=3, r_off=1, seed=8),
+    "random_pattern": dict(Lx=7, Ly=6, N=9, r_diag=2, r_off=1, seed=10, random_density=0.3),
 }
 
 
@@ -48,6 +51,13 @@ def rel_err(got, ref):
     elem = float(np.max(np.abs(got - ref) / scale))
     norm = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
     return max(elem, norm)
+
+
+def sol_err(got, ref):
+    """Norm-wise relative difference, used for solver outputs."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
 def to_component_major(v, nc, b):

@@ -12,7 +12,7 @@ import oracle
 from paper_2403_09198_gb300 import inputs
 from paper_2403_09198_gb300.binding import StsError, StsJacobian
 from tests._gpu import (SMALL, TOL64, dev, from_component_major, host, oracle_jac, rel_err,
-                        to_component_major, workload)
+                        sol_err, to_component_major, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -174,12 +174,14 @@ def test_gmres_parity(case):
     ho = np.array(io["history"])
     n = min(len(ho), len(ig.history))
     keep = ho[:n] > 1e-13
-    # 1e-8 relative while the residual is above 1e-13, plus an absolute floor
-    # of 1e-18 (in units of ||b||), far below the rounding level of either solver
-    np.testing.assert_allclose(ig.history[:n][keep], ho[:n][keep], rtol=1e-8, atol=1e-18)
+    # 1e-8 relative while the residual is above 1e-13, plus an absolute floor of
+    # 1e-15 (about 5 eps in units of ||b||): two backward-stable solvers that
+    # orthogonalise differently (CGS2 here, MGS in the oracle) may differ by
+    # O(eps ||b||) in the rotated residual, and that difference survives restarts
+    np.testing.assert_allclose(ig.history[:n][keep], ho[:n][keep], rtol=1e-8, atol=1e-15)
     xg2, _ = jac.gmres(dev(w.rhs), restart=m, rtol=1e-14, max_iters=400)
     xo2, _ = oracle.gmres(J, w.rhs, restart=m, rtol=1e-14, max_iters=400)
-    assert np.linalg.norm(host(xg2) - xo2) / np.linalg.norm(xo2) <= TOL64
+    assert sol_err(host(xg2), xo2) <= TOL64
     jac.close()
 
 
@@ -188,15 +190,16 @@ def test_gmres_host_vectors_transposed_and_unpreconditioned():
     J = oracle_jac(w)
     jac = _jac(w, transpose=True)
     jac.bjacobi_setup()
-    x, info = jac.gmres(w.rhs.copy(), rtol=1e-12)                 # host vectors
+    # solutions: both solvers to rtol 1e-14, norm-wise agreement 1e-12
+    x, info = jac.gmres(w.rhs.copy(), rtol=1e-14)                 # host vectors
     assert isinstance(x, np.ndarray) and info.converged
-    assert rel_err(x, oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
-    xt, it = jac.gmres(dev(w.rhs), rtol=1e-12, trans=True)
+    assert sol_err(x, oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= TOL64
+    xt, it = jac.gmres(dev(w.rhs), rtol=1e-14, trans=True)
     assert it.converged
-    assert rel_err(host(xt), oracle.gmres(J, w.rhs, rtol=1e-14, trans=True)[0]) <= 1e-10
-    xn, inn = jac.gmres(dev(w.rhs), rtol=1e-12, precond="none", restart=60)
+    assert sol_err(host(xt), oracle.gmres(J, w.rhs, rtol=1e-14, trans=True)[0]) <= TOL64
+    xn, inn = jac.gmres(dev(w.rhs), rtol=1e-14, precond="none", restart=60)
     assert inn.converged
-    assert rel_err(host(xn), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
+    assert sol_err(host(xn), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= TOL64
     jac.close()
 
 
@@ -360,9 +363,9 @@ def test_dense_bsr_baseline(name):
     assert rel_err(host(jac.matvec(dev(x))), oracle.matvec(J, x)) <= TOL64
     jac.bjacobi_setup()
     assert rel_err(host(jac.bjacobi_apply(dev(x))), oracle.bj_apply(oracle.bj_setup(J), x)) <= TOL64
-    xs, info = jac.gmres(dev(w.rhs), rtol=1e-12)
+    xs, info = jac.gmres(dev(w.rhs), rtol=1e-14)
     assert info.converged
-    assert rel_err(host(xs), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= 1e-10
+    assert sol_err(host(xs), oracle.gmres(J, w.rhs, rtol=1e-14)[0]) <= TOL64
     jac.close()
 
 
