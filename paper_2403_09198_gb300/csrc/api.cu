@@ -39,6 +39,34 @@ sts_status dev_alloc(sts_jac_s *h, void **p, size_t bytes) {
     return STS_OK;
 }
 
+// Band half-width w if rows p < N = b - kStructNF hold exactly the level band
+// |p - q| <= w followed by the kStructNF flow columns and the last kStructNF
+// rows are dense; -1 if the pattern is not of that family.
+int struct_band(int b, const std::vector<int> &ptr, const std::vector<int> &idx) {
+    const int N = b - kStructNF;
+    if (N < 1) return -1;
+    for (int r = N; r < b; ++r) {
+        if (ptr[r + 1] - ptr[r] != b) return -1;
+        for (int e = ptr[r]; e < ptr[r + 1]; ++e)
+            if (idx[e] != e - ptr[r]) return -1;
+    }
+    for (int w = 0; w <= kStructMaxW; ++w) {
+        bool ok = true;
+        for (int p = 0; p < N && ok; ++p) {
+            const int lo = std::max(0, p - w), hi = std::min(N - 1, p + w);
+            if (ptr[p + 1] - ptr[p] != (hi - lo + 1) + kStructNF) {
+                ok = false;
+                break;
+            }
+            int e = ptr[p];
+            for (int q = lo; q <= hi; ++q, ++e) ok = ok && idx[e] == q;
+            for (int f = 0; f < kStructNF; ++f, ++e) ok = ok && idx[e] == N + f;
+        }
+        if (ok) return w;
+    }
+    return -1;
+}
+
 namespace {
 
 sts_status check_csr(const int *ptr, const int *idx, int rows, int cols, bool need_diag, const char *what) {
@@ -78,34 +106,6 @@ void transpose_pattern(int b, const std::vector<int> &ptr, const std::vector<int
             tidx[t] = p;
             src[t] = e;
         }
-}
-
-// Band half-width w if rows p < N = b - kStructNF hold exactly the level band
-// |p - q| <= w followed by the kStructNF flow columns and the last kStructNF
-// rows are dense; -1 if the pattern is not of that family.
-int struct_band(int b, const std::vector<int> &ptr, const std::vector<int> &idx) {
-    const int N = b - kStructNF;
-    if (N < 1) return -1;
-    for (int r = N; r < b; ++r) {
-        if (ptr[r + 1] - ptr[r] != b) return -1;
-        for (int e = ptr[r]; e < ptr[r + 1]; ++e)
-            if (idx[e] != e - ptr[r]) return -1;
-    }
-    for (int w = 0; w <= kStructMaxW; ++w) {
-        bool ok = true;
-        for (int p = 0; p < N && ok; ++p) {
-            const int lo = std::max(0, p - w), hi = std::min(N - 1, p + w);
-            if (ptr[p + 1] - ptr[p] != (hi - lo + 1) + kStructNF) {
-                ok = false;
-                break;
-            }
-            int e = ptr[p];
-            for (int q = lo; q <= hi; ++q, ++e) ok = ok && idx[e] == q;
-            for (int f = 0; f < kStructNF; ++f, ++e) ok = ok && idx[e] == N + f;
-        }
-        if (ok) return w;
-    }
-    return -1;
 }
 
 // Build the plan of one matvec direction (dir 0: y = J x, dir 1: y = J^T x).

@@ -315,6 +315,204 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Structured apply for the paper's pattern family (level band of half-width W
+// plus NF = 3 dense flow rows / columns).  Its LU has no fill:
+//   L: level row i holds the band (i, i-W..i-1); flow rows are dense.
+//   U: level row i holds (i, i..i+W) and the flow columns; the flow block is
+//      upper triangular.
+// Both directions are "forward unit-lower arrow-band sweep, then backward
+// scaled unit-upper arrow-band sweep" over a per-direction coefficient stream:
+//   forward level row i:  W band coefficients (oldest first), then the NF
+//                          coefficients of the flow rows in column i, which
+//                          feed NF independent accumulators;
+//   forward flow rows:    the 3 coefficients among the flow unknowns;
+//   backward flow rows:   pivot inverse and coefficients, then the r dot-vector
+//                          entries of t = V^T x0 for that unknown;
+//   backward level row i: pivot inverse, NF flow coefficients, W band
+//                          coefficients (farthest first), r dot-vector entries;
+//   tail:                 W[a][q] for the correction x = x0 - W C^-1 t.
+// The band recurrences keep their last W values in registers, so the only
+// dependency chain is one FMA per row.
+template <typename T>
+struct SApplyArgs {
+    const T *st;            // [len][ncp]
+    const double *Cinv;     // [r][r][ncp]
+    const T *x;
+    T *y;
+    int len, b, N, r, ncp, trans;
+};
+
+template <typename T, int W, int RMAX>
+__global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
+    constexpr int NF = kStructNF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
+    T *ws = stg + kApStages * kApStage * kTile;                 // [b][32]: w, then x0
+    constexpr int PIECES = kTile * (int)sizeof(T) / 16;
+    constexpr int PER_ITER = kTile / PIECES;
+    const int lane = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int cell = tile * kTile + lane;
+    const size_t P = a.ncp;
+    const int L = a.len, N = a.N, r = a.r;
+    const int nchunks = (L + kApStage - 1) / kApStage;
+    const T *__restrict__ stream = a.st + (size_t)tile * kTile;
+    auto issue = [&](int c) {
+        T *dst0 = stg + (c % kApStages) * kApStage * kTile;
+        const int piece = lane % PIECES;
+#pragma unroll
+        for (int it = 0; it < kApStage / PER_ITER; ++it) {
+            const int pos = it * PER_ITER + lane / PIECES;
+            const int gp = c * kApStage + pos;
+            if (gp < L)
+                cp_async16(dst0 + pos * kTile + piece * (16 / (int)sizeof(T)),
+                           stream + (size_t)gp * P + piece * (16 / (int)sizeof(T)));
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int c = 0; c < kApStages - 1; ++c) {
+        if (c < nchunks) issue(c);
+        else cp_async_commit();
+    }
+    const T *__restrict__ x = a.x;
+    for (int i = 0; i < a.b; ++i) ws[i * kTile + lane] = __ldg(x + i * P + cell);
+    int ch = 0, off = 0;
+    const T *cur = nullptr;
+    auto enter = [&](int c) {
+        cp_async_wait<kApStages - 2>();
+        __syncwarp();
+        if (c + kApStages - 1 < nchunks) issue(c + kApStages - 1);
+        else cp_async_commit();
+        cur = stg + (c % kApStages) * kApStage * kTile + lane;
+    };
+    enter(0);
+    auto next = [&]() -> T {
+        if (off == kApStage) {
+            ++ch;
+            off = 0;
+            enter(ch);
+        }
+        return cur[(off++) * kTile];
+    };
+    // forward sweep
+    T win[W > 0 ? W : 1];
+#pragma unroll
+    for (int k = 0; k < W; ++k) win[k] = T(0);
+    T accf[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) accf[f] = T(0);
+    for (int i = 0; i < N; ++i) {
+        T acc = ws[i * kTile + lane];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc = fma(-next(), win[k], acc);
+        ws[i * kTile + lane] = acc;
+#pragma unroll
+        for (int k = 0; k + 1 < W; ++k) win[k] = win[k + 1];
+        if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) accf[f] = fma(next(), acc, accf[f]);
+    }
+    T wf[NF];
+    wf[0] = ws[N * kTile + lane] - accf[0];
+    wf[1] = fma(-next(), wf[0], ws[(N + 1) * kTile + lane] - accf[1]);
+    {
+        const T c0 = next(), c1 = next();
+        wf[2] = fma(-c1, wf[1], fma(-c0, wf[0], ws[(N + 2) * kTile + lane] - accf[2]));
+    }
+    // backward sweep with t = V^T x0 accumulated on the way
+    T t[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) t[k] = T(0);
+    T xf[NF];
+    xf[2] = next() * wf[2];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k)
+        if (k < r) t[k] = fma(next(), xf[2], t[k]);
+    xf[1] = next() * wf[1];
+    xf[1] = fma(-next(), xf[2], xf[1]);
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k)
+        if (k < r) t[k] = fma(next(), xf[1], t[k]);
+    xf[0] = next() * wf[0];
+    xf[0] = fma(-next(), xf[1], xf[0]);
+    xf[0] = fma(-next(), xf[2], xf[0]);
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k)
+        if (k < r) t[k] = fma(next(), xf[0], t[k]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) ws[(N + f) * kTile + lane] = xf[f];
+    T xw[W > 0 ? W : 1];
+#pragma unroll
+    for (int k = 0; k < W; ++k) xw[k] = T(0);
+    for (int i = N - 1; i >= 0; --i) {
+        T acc = next() * ws[i * kTile + lane];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc = fma(-next(), xf[f], acc);
+#pragma unroll
+        for (int k = W - 1; k >= 0; --k) acc = fma(-next(), xw[k], acc);
+        ws[i * kTile + lane] = acc;
+#pragma unroll
+        for (int k = W - 1; k > 0; --k) xw[k] = xw[k - 1];
+        if (W > 0) xw[0] = acc;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k)
+            if (k < r) t[k] = fma(next(), acc, t[k]);
+    }
+    // z = C^-1 t in FP64, then x = x0 - W z
+    T z[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+        double sacc = 0.0;
+        if (k < r) {
+#pragma unroll
+            for (int l = 0; l < RMAX; ++l)
+                if (l < r) {
+                    const double cij = a.trans ? __ldg(a.Cinv + ((size_t)l * r + k) * P + cell)
+                                               : __ldg(a.Cinv + ((size_t)k * r + l) * P + cell);
+                    sacc = fma(cij, (double)t[l], sacc);
+                }
+        }
+        z[k] = (T)sacc;
+    }
+    for (int q = 0; q < a.b; ++q) {
+        T v = ws[q * kTile + lane];
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k)
+            if (k < r) v = fma(-next(), z[k], v);
+        a.y[q * P + cell] = v;
+    }
+    cp_async_wait<0>();
+}
+
+// Structured stream packing: per position a source code and argument
+//   src >= 0: LU slot (times the pivot inverse of row arg if arg >= 0)
+//   src = -1: pivot inverse of row arg      src = -2: dot vector entry arg
+//   src = -3: W entry arg                   src = -4: zero
+template <typename T>
+__global__ void k_smw_spack(T *out, const double *lu, const double *dinv, const double *DV, const double *WW,
+                            const int *src, const int *arg, int len, int ncp) {
+    const long long total = (long long)len * ncp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cell = (int)(i % ncp), pos = (int)(i / ncp);
+        const int sv = src[pos], ag = arg[pos];
+        double v = 0.0;
+        if (sv >= 0) {
+            v = lu[(size_t)sv * ncp + cell];
+            if (ag >= 0) v *= dinv[(size_t)ag * ncp + cell];
+        } else if (sv == -1) {
+            v = dinv[(size_t)ag * ncp + cell];
+        } else if (sv == -2) {
+            v = DV[(size_t)ag * ncp + cell];
+        } else if (sv == -3) {
+            v = WW[(size_t)ag * ncp + cell];
+        }
+        out[i] = (T)v;
+    }
+}
+
 // Repack diagonal-block values into [entry][cell] and the diagonal pairs into [k][q][cell].
 __global__ void k_smw_repack(double *Sd, double *Ud, double *Vd, const double *S, const double *U,
                              const double *V, const int *diag_blk, const long long *soff,
@@ -477,6 +675,66 @@ sts_status smw_build(sts_jac_s *h) {
         if (desc.size() != pk_slot.size()) return set_error(STS_ERR_INVALID_ARG, "internal: apply program size");
         STS_TRY(upload(h, &M.ap_desc[dir], desc));
     }
+    // structured apply tables (both directions)
+    const int sw = struct_band(b, h->dptr, h->didx);
+    M.structured = sw >= 0 && h->r_diag <= 4 && M.nnz_lu == h->nnz_d;
+    if (M.structured) {
+        const int NF = kStructNF, N = b - NF, r = h->r_diag;
+        M.s_w = sw;
+        auto sl = [&](int i, int j) { return slot[(size_t)i * b + j]; };
+        for (int dir = 0; dir < 2; ++dir) {
+            std::vector<int> src, arg;
+            auto put = [&](int s_, int a_) { src.push_back(s_); arg.push_back(a_); };
+            // lower factor of this direction: dir 0 L, dir 1 U'^T (U scaled by the row pivot inverse)
+            auto lo = [&](int i, int j) {           // coefficient (i, j), i > j
+                if (dir == 0) put(sl(i, j), -1);
+                else put(sl(j, i), j);
+            };
+            // upper factor after the pivot scaling: dir 0 U' = D^-1 U, dir 1 L^T
+            auto up = [&](int i, int j) {           // coefficient (i, j), i < j
+                if (dir == 0) put(sl(i, j), i);
+                else put(sl(j, i), -1);
+            };
+            for (int i = 0; i < N; ++i) {
+                for (int k = 0; k < sw; ++k) {
+                    const int j = i - sw + k;
+                    if (j >= 0) lo(i, j);
+                    else put(-4, 0);
+                }
+                for (int f = 0; f < NF; ++f) lo(N + f, i);
+            }
+            lo(N + 1, N);
+            lo(N + 2, N);
+            lo(N + 2, N + 1);
+            put(-1, N + 2);
+            for (int k = 0; k < r; ++k) put(-2, k * b + N + 2);
+            put(-1, N + 1);
+            up(N + 1, N + 2);
+            for (int k = 0; k < r; ++k) put(-2, k * b + N + 1);
+            put(-1, N);
+            up(N, N + 1);
+            up(N, N + 2);
+            for (int k = 0; k < r; ++k) put(-2, k * b + N);
+            for (int i = N - 1; i >= 0; --i) {
+                put(-1, i);
+                for (int f = 0; f < NF; ++f) up(i, N + f);
+                for (int k = sw - 1; k >= 0; --k) {
+                    const int j = i + 1 + k;
+                    if (j < N) up(i, j);
+                    else put(-4, 0);
+                }
+                for (int k = 0; k < r; ++k) put(-2, k * b + i);
+            }
+            for (int q = 0; q < b; ++q)
+                for (int k = 0; k < r; ++k) put(-3, k * b + q);
+            for (size_t e = 0; e < src.size(); ++e)
+                if (src[e] < -4 || (src[e] >= 0 && src[e] >= M.nnz_lu))
+                    return set_error(STS_ERR_INVALID_ARG, "internal: structured apply table");
+            M.s_len = (int)src.size();
+            STS_TRY(upload(h, &M.spk_src[dir], src));
+            STS_TRY(upload(h, &M.spk_arg[dir], arg));
+        }
+    }
     STS_TRY(upload(h, &M.lu_diag, M.h_lu_diag));
     STS_TRY(upload(h, &M.src_slot, M.h_src_slot));
     STS_TRY(upload(h, &M.d_ptr, h->dptr));
@@ -497,7 +755,7 @@ sts_status smw_build(sts_jac_s *h) {
     STS_TRY(dalloc(h, &M.Cinv, (size_t)std::max(r * r, 1) * P));
     for (int dir = 0; dir < 2; ++dir) {
         if (dir == 1 && !h->has_T) continue;
-        const size_t len = (size_t)M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const size_t len = M.structured ? (size_t)M.s_len : (size_t)M.n_fwd[dir] + M.n_bwd[dir] + b;
         STS_TRY(dalloc(h, &M.ap64[dir], len * P));
         if (h->dtype == STS_MIXED) {
             STS_TRY(dalloc(h, &M.ap32[dir], len * P));
@@ -556,8 +814,23 @@ sts_status smw_setup(sts_jac_s *h) {
     const int b = h->b, r = h->r_diag;
     for (int dir = 0; dir < 2; ++dir) {
         if (dir == 1 && !h->has_T) continue;
-        const int len = M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const double *DV = dir == 0 ? M.Vd : M.Ud;
+        const double *WW = dir == 0 ? M.W : M.Wt;
+        const int len = M.structured ? M.s_len : M.n_fwd[dir] + M.n_bwd[dir] + b;
         const long long n = (long long)len * P;
+        if (M.structured) {
+            k_smw_spack<double><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, DV, WW,
+                                                                          M.spk_src[dir], M.spk_arg[dir], len,
+                                                                          h->ncp);
+            STS_LAUNCHED();
+            if (M.ap32[dir]) {
+                k_smw_spack<float><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap32[dir], M.lu, M.dinv, DV, WW,
+                                                                            M.spk_src[dir], M.spk_arg[dir], len,
+                                                                            h->ncp);
+                STS_LAUNCHED();
+            }
+            continue;
+        }
         k_smw_pack<double><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, M.pk_slot[dir],
                                                                      M.pk_scale[dir], len, h->ncp);
         STS_LAUNCHED();
@@ -567,9 +840,9 @@ sts_status smw_setup(sts_jac_s *h) {
             STS_LAUNCHED();
             const long long nw = (long long)r * b * P;
             if (nw > 0) {
-                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.W32[dir], dir == 0 ? M.W : M.Wt, nw);
+                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.W32[dir], WW, nw);
                 STS_LAUNCHED();
-                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.DV32[dir], dir == 0 ? M.Vd : M.Ud, nw);
+                k_round<float><<<grid_for(nw, 256), 256, 0, h->stream>>>(M.DV32[dir], DV, nw);
                 STS_LAUNCHED();
             }
         }
@@ -594,13 +867,37 @@ static sts_status smw_apply_t(sts_jac_s *h, int dir, const T *st, const T *dv, c
     return STS_OK;
 }
 
+template <typename T>
+static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T *z) {
+    const SmwPlan &M = h->smw;
+    SApplyArgs<T> a;
+    a.st = st; a.Cinv = M.Cinv; a.x = x; a.y = z;
+    a.len = M.s_len; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp; a.trans = dir;
+    const size_t smem = ((size_t)kApStages * kApStage + h->b) * kTile * sizeof(T);
+    void (*kern)(SApplyArgs<T>) = nullptr;
+    const bool r2 = a.r <= 2;
+    switch (M.s_w) {
+        case 0: kern = r2 ? k_smw_sapply<T, 0, 2> : k_smw_sapply<T, 0, 4>; break;
+        case 1: kern = r2 ? k_smw_sapply<T, 1, 2> : k_smw_sapply<T, 1, 4>; break;
+        case 2: kern = r2 ? k_smw_sapply<T, 2, 2> : k_smw_sapply<T, 2, 4>; break;
+        case 3: kern = r2 ? k_smw_sapply<T, 3, 2> : k_smw_sapply<T, 3, 4>; break;
+        default: kern = r2 ? k_smw_sapply<T, 4, 2> : k_smw_sapply<T, 4, 4>; break;
+    }
+    if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<h->n_tiles, kTile, smem, h->stream>>>(a);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
 sts_status smw_apply64(sts_jac_s *h, int dir, const double *x, double *z) {
     const SmwPlan &M = h->smw;
+    if (M.structured) return smw_sapply_t<double>(h, dir, M.ap64[dir], x, z);
     return smw_apply_t<double>(h, dir, M.ap64[dir], dir == 0 ? M.Vd : M.Ud, dir == 0 ? M.W : M.Wt, x, z);
 }
 
 sts_status smw_apply32(sts_jac_s *h, int dir, const float *x, float *z) {
     const SmwPlan &M = h->smw;
+    if (M.structured) return smw_sapply_t<float>(h, dir, M.ap32[dir], x, z);
     return smw_apply_t<float>(h, dir, M.ap32[dir], M.DV32[dir], M.W32[dir], x, z);
 }
 

@@ -178,6 +178,12 @@ struct SmwPlan {
     float *DV32[2] = {nullptr, nullptr};    // Vd, Ud rounded (dot vectors of the two directions)
     int *err_cell = nullptr;     // device: first failing cell (INT_MAX if none)
     bool ready = false;
+    // Structured apply (diagonal pattern of the paper's family, no fill): one
+    // coefficient stream per direction in ap64/ap32 of length s_len, packed
+    // from (spk_src, spk_arg) (see k_smw_spack).
+    bool structured = false;
+    int s_w = 0, s_len = 0;
+    int *spk_src[2] = {nullptr, nullptr}, *spk_arg[2] = {nullptr, nullptr};
 };
 
 // Dense-BSR baseline (Section 3.4 storage).
@@ -237,6 +243,9 @@ struct sts_jac_s {
 };
 
 namespace sts {
+
+// Band half-width of a pattern of the structured family, or -1 (api.cu).
+int struct_band(int b, const std::vector<int> &ptr, const std::vector<int> &idx);
 
 // allocation helpers (api.cu)
 sts_status dev_alloc(sts_jac_s *h, void **p, size_t bytes);
