@@ -14,6 +14,7 @@
 
 #include <type_traits>
 
+#include "ring.cuh"
 #include "sts_internal.h"
 
 namespace sts {
@@ -42,6 +43,10 @@ struct MvArgs {
 // Chunk of stream positions held in registers.
 template <typename T> struct Chunk { static constexpr int CH = 8; };
 template <> struct Chunk<float> { static constexpr int CH = 16; };
+
+// Shared-memory ring of the structured level rows: stages of kMvStage positions.
+constexpr int kMvStage = 8;
+constexpr int kMvStages = 4;
 
 // Pass 1: one warp per (tile, dot task); lane = cell.  A dot task is one
 // length-b dot product  c = d . x_j  with j the neighbour of the task's slot:
@@ -167,14 +172,12 @@ template <typename T, int WD>
 __global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
     constexpr int NF = kStructNF;
     constexpr int NS = kStructMaxSlots;
-    constexpr int RD = 2 * WD + 1 + NF;          // diagonal-slot entries of a level row
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wid >= (long long)a.n_tiles * a.n_groups) return;
     const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
     const int ns = a.n_slots, nps = a.n_pslots, N = a.sN;
     const size_t ncp = a.ncp;
-    const unsigned mask = a.slot_mask[t];
     const size_t cell = (size_t)t * kTile + lane;
     const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
     const T *__restrict__ tile_stream = a.main + (size_t)t * a.tile_len * kTile + lane;
@@ -201,29 +204,34 @@ __global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
         for (int f = 0; f < NF; ++f) xf[s][f] = s < ns ? __ldg(xs[s] + (size_t)(N + f) * ncp) : T(0);
     }
     const int p0 = g * a.s_gl, p1 = min(N, p0 + a.s_gl);
+    // the group's rows are contiguous in the stream: stream them through this
+    // warp's shared-memory ring
+    extern __shared__ __align__(16) unsigned char mv_smem[];
+    T *ring_mem = reinterpret_cast<T *>(mv_smem) + (size_t)(threadIdx.x >> 5) * kMvStages * kMvStage * kTile;
+    Ring<T, kMvStage, kMvStages> R;
+    R.start(ring_mem, a.main + ((size_t)t * a.tile_len + (size_t)p0 * a.s_rl) * kTile, kTile,
+            (p1 - p0) * a.s_rl, lane);
     for (int p = p0; p < p1; ++p) {
-        const T *__restrict__ sr = tile_stream + (size_t)p * a.s_rl * kTile;
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k <= 2 * WD; ++k) {
             const int q = min(max(p - WD + k, 0), N - 1);    // clipped band entries carry zeros
-            acc = fma(__ldg(sr + (size_t)k * kTile), __ldg(xs[0] + (size_t)q * ncp), acc);
+            acc = fma(R.next(), __ldg(xs[0] + (size_t)q * ncp), acc);
         }
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc = fma(__ldg(sr + (size_t)(2 * WD + 1 + f) * kTile), xf[0][f], acc);
+        for (int f = 0; f < NF; ++f) acc = fma(R.next(), xf[0][f], acc);
 #pragma unroll
         for (int s = 1; s < NS; ++s) {
-            if (s < ns && ((mask >> s) & 1u)) {
-                const T *__restrict__ so = sr + (size_t)(RD + (s - 1) * (1 + NF)) * kTile;
-                acc = fma(__ldg(so), __ldg(xs[s] + (size_t)p * ncp), acc);
+            if (s < ns) {
+                acc = fma(R.next(), __ldg(xs[s] + (size_t)p * ncp), acc);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) acc = fma(__ldg(so + (size_t)(1 + f) * kTile), xf[s][f], acc);
+                for (int f = 0; f < NF; ++f) acc = fma(R.next(), xf[s][f], acc);
             }
         }
-        const T *__restrict__ su = sr + (size_t)(RD + (ns - 1) * (1 + NF)) * kTile;
-        for (int k = 0; k < nps; ++k) acc = fma(__ldg(su + (size_t)k * kTile), __ldg(cc + (size_t)k * kTile), acc);
+        for (int k = 0; k < nps; ++k) acc = fma(R.next(), __ldg(cc + (size_t)k * kTile), acc);
         a.y[(size_t)p * ncp + cell] = acc;
     }
+    R.finish();
 }
 
 // Repack the public values into one stream of one direction.  Each stream
@@ -369,13 +377,17 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
     const long long warps = (long long)a.n_tiles * a.n_groups;
     const unsigned grid = (unsigned)((warps + 3) / 4);
     if (a.structured) {
+        const size_t smem = (size_t)4 * kMvStages * kMvStage * kTile * sizeof(T);
+        void (*kern)(MvArgs<T>) = nullptr;
         switch (a.wd) {
-            case 0: k_mv_struct<T, 0><<<grid, 128, 0, h->stream>>>(a); break;
-            case 1: k_mv_struct<T, 1><<<grid, 128, 0, h->stream>>>(a); break;
-            case 2: k_mv_struct<T, 2><<<grid, 128, 0, h->stream>>>(a); break;
-            case 3: k_mv_struct<T, 3><<<grid, 128, 0, h->stream>>>(a); break;
-            default: k_mv_struct<T, 4><<<grid, 128, 0, h->stream>>>(a); break;
+            case 0: kern = k_mv_struct<T, 0>; break;
+            case 1: kern = k_mv_struct<T, 1>; break;
+            case 2: kern = k_mv_struct<T, 2>; break;
+            case 3: kern = k_mv_struct<T, 3>; break;
+            default: kern = k_mv_struct<T, 4>; break;
         }
+        if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, 128, smem, h->stream>>>(a);
     } else {
         k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);
     }

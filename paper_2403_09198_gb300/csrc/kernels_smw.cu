@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "ring.cuh"
 #include "sts_internal.h"
 
 namespace sts {
@@ -206,14 +207,6 @@ struct ApplyArgs {
 constexpr int kApStage = 32;    // stream positions per shared-memory stage
 constexpr int kApStages = 3;    // stages in flight (two ahead of the one consumed)
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // One warp per 32 cells, one lane per cell.  The tile's apply stream is
 // copied into a ring of shared-memory stages with cp.async two stages ahead of
 // its use; the working vector lives in shared memory [q][lane]; the triangular
@@ -223,60 +216,29 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
     T *w = stg + kApStages * kApStage * kTile;                  // [b][32]
-    constexpr int PIECES = kTile * (int)sizeof(T) / 16;         // 16-byte pieces per position
-    constexpr int PER_ITER = kTile / PIECES;                    // positions per warp-wide copy
     const int lane = threadIdx.x;
     const int tile = blockIdx.x;
     const int cell = tile * kTile + lane;
     const size_t P = a.ncp;
-    const int L = a.len;
-    const int nchunks = (L + kApStage - 1) / kApStage;
-    const T *__restrict__ stream = a.st + (size_t)tile * kTile;
-    auto issue = [&](int c) {
-        T *dst0 = stg + (c % kApStages) * kApStage * kTile;
-        const int piece = lane % PIECES;
-#pragma unroll
-        for (int it = 0; it < kApStage / PER_ITER; ++it) {
-            const int pos = it * PER_ITER + lane / PIECES;
-            const int gp = c * kApStage + pos;
-            if (gp < L)
-                cp_async16(dst0 + pos * kTile + piece * (16 / (int)sizeof(T)),
-                           stream + (size_t)gp * P + piece * (16 / (int)sizeof(T)));
-        }
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int c = 0; c < kApStages - 1; ++c) {
-        if (c < nchunks) issue(c);
-        else cp_async_commit();
-    }
     const T *__restrict__ x = a.x;
+    Ring<T, kApStage, kApStages> R;
+    R.start(stg, a.st + (size_t)tile * kTile, P, a.len, lane);
     for (int i = 0; i < a.b; ++i) w[i * kTile + lane] = __ldg(x + i * P + cell);
     const unsigned *__restrict__ dd = a.desc;
     T acc = T(0);
-    for (int c = 0; c < nchunks; ++c) {
-        cp_async_wait<kApStages - 2>();
-        __syncwarp();
-        if (c + kApStages - 1 < nchunks) issue(c + kApStages - 1);
-        else cp_async_commit();
-        const T *cur = stg + (c % kApStages) * kApStage * kTile + lane;
-        const unsigned *dc = dd + c * kApStage;
-        const int n_in = min(kApStage, L - c * kApStage);
-#pragma unroll 8
-        for (int i = 0; i < n_in; ++i) {
-            const unsigned d = __ldg(dc + i);
-            const T v = cur[i * kTile];
-            const int row = (d >> 12) & 0xfffu, col = d & 0xfffu;
-            if (d & kApScale) {
-                acc = v * w[row * kTile + lane];
-            } else {
-                if (d & kApBegin) acc = w[row * kTile + lane];
-                acc = fma(-v, w[col * kTile + lane], acc);
-            }
-            if (d & kApEnd) w[row * kTile + lane] = acc;
+    for (int i = 0; i < a.len; ++i) {
+        const unsigned d = __ldg(dd + i);
+        const T v = R.next();
+        const int row = (d >> 12) & 0xfffu, col = d & 0xfffu;
+        if (d & kApScale) {
+            acc = v * w[row * kTile + lane];
+        } else {
+            if (d & kApBegin) acc = w[row * kTile + lane];
+            acc = fma(-v, w[col * kTile + lane], acc);
         }
+        if (d & kApEnd) w[row * kTile + lane] = acc;
     }
-    cp_async_wait<0>();
+    R.finish();
     // t = dv^T x0, z = C^-1 t (FP64), x = x0 - W z
     T t[RMAX];
 #pragma unroll
@@ -349,53 +311,16 @@ __global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
     T *ws = stg + kApStages * kApStage * kTile;                 // [b][32]: w, then x0
-    constexpr int PIECES = kTile * (int)sizeof(T) / 16;
-    constexpr int PER_ITER = kTile / PIECES;
     const int lane = threadIdx.x;
     const int tile = blockIdx.x;
     const int cell = tile * kTile + lane;
     const size_t P = a.ncp;
-    const int L = a.len, N = a.N, r = a.r;
-    const int nchunks = (L + kApStage - 1) / kApStage;
-    const T *__restrict__ stream = a.st + (size_t)tile * kTile;
-    auto issue = [&](int c) {
-        T *dst0 = stg + (c % kApStages) * kApStage * kTile;
-        const int piece = lane % PIECES;
-#pragma unroll
-        for (int it = 0; it < kApStage / PER_ITER; ++it) {
-            const int pos = it * PER_ITER + lane / PIECES;
-            const int gp = c * kApStage + pos;
-            if (gp < L)
-                cp_async16(dst0 + pos * kTile + piece * (16 / (int)sizeof(T)),
-                           stream + (size_t)gp * P + piece * (16 / (int)sizeof(T)));
-        }
-        cp_async_commit();
-    };
-#pragma unroll
-    for (int c = 0; c < kApStages - 1; ++c) {
-        if (c < nchunks) issue(c);
-        else cp_async_commit();
-    }
+    const int N = a.N, r = a.r;
+    Ring<T, kApStage, kApStages> R;
+    R.start(stg, a.st + (size_t)tile * kTile, P, a.len, lane);
     const T *__restrict__ x = a.x;
     for (int i = 0; i < a.b; ++i) ws[i * kTile + lane] = __ldg(x + i * P + cell);
-    int ch = 0, off = 0;
-    const T *cur = nullptr;
-    auto enter = [&](int c) {
-        cp_async_wait<kApStages - 2>();
-        __syncwarp();
-        if (c + kApStages - 1 < nchunks) issue(c + kApStages - 1);
-        else cp_async_commit();
-        cur = stg + (c % kApStages) * kApStage * kTile + lane;
-    };
-    enter(0);
-    auto next = [&]() -> T {
-        if (off == kApStage) {
-            ++ch;
-            off = 0;
-            enter(ch);
-        }
-        return cur[(off++) * kTile];
-    };
+    auto next = [&]() -> T { return R.next(); };
     // forward sweep
     T win[W > 0 ? W : 1];
 #pragma unroll
@@ -483,7 +408,7 @@ __global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
             if (k < r) v = fma(-next(), z[k], v);
         a.y[q * P + cell] = v;
     }
-    cp_async_wait<0>();
+    R.finish();
 }
 
 // Structured stream packing: per position a source code and argument
