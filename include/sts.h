@@ -176,6 +176,29 @@ sts_status sts_jac_update_values(sts_jac_t h, const double *S, const double *U,
  */
 sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans);
 
+/*
+ * The same product as sts_jac_matvec (same arguments, same result), for
+ * callers that must not allocate device memory while they run: code that has
+ * reserved all device memory up front under a fixed budget, or that cannot
+ * afford cudaMalloc / cudaFree, which may synchronise the whole device, in the
+ * middle of its stream work.  This call allocates nothing: the per-block dot
+ * products of the first pass go to a library-owned static device buffer of
+ * 4 MiB (2^19 doubles) instead of handle memory.  That buffer exists on every
+ * GPU that loads the library until the process exits.
+ *
+ * Limit: the handle needs ceil(n_cells / 32) x (dot tasks per cell) x 32
+ * doubles of scratch, at most 2^19 (for example 16384 cells with 21 dot tasks,
+ * the 128x128, N = 60 workload, use 344064); larger handles get
+ * STS_ERR_INVALID_ARG and should use sts_jac_matvec.
+ * The first call made on a device (with that device current) looks up the
+ * buffer's address with cudaGetSymbolAddress; make that first call before
+ * any stream capture.  All calls share the one buffer: calls that overlap on
+ * the GPU (different streams or threads) race on it and must be serialised by
+ * the caller.  Factored representation only; trans = 1 needs enable_transpose.
+ * The paper has no counterpart to this entry point.  Asynchronous.
+ */
+sts_status sts_jac_matvec_noalloc(sts_jac_t h, const double *x, double *y, int trans);
+
 /* FP32 operator, FP32 device vectors (needs dtype STS_MIXED).  Asynchronous. */
 sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans);
 

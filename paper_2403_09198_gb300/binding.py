@@ -27,7 +27,7 @@ STS_PRECOND_BJ, STS_PRECOND_NONE = 0, 1
 
 # Every entry point declared in include/sts.h.
 ABI_FUNCTIONS = ["sts_last_error", "sts_version", "sts_jac_create", "sts_jac_update_values",
-                 "sts_jac_matvec", "sts_jac_matvec_f32", "sts_jac_bjacobi_setup",
+                 "sts_jac_matvec", "sts_jac_matvec_noalloc", "sts_jac_matvec_f32", "sts_jac_bjacobi_setup",
                  "sts_jac_bjacobi_apply", "sts_jac_bjacobi_apply_f32", "sts_gmres_solve",
                  "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_jac_destroy"]
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                 "sts_jac_create": [ctypes.POINTER(sts_jac_desc), ctypes.POINTER(P)],
                 "sts_jac_update_values": [P, P, P, P, I],
                 "sts_jac_matvec": [P, P, P, I],
+                "sts_jac_matvec_noalloc": [P, P, P, I],
                 "sts_jac_matvec_f32": [P, P, P, I],
                 "sts_jac_bjacobi_setup": [P],
                 "sts_jac_bjacobi_apply": [P, P, P, I],

@@ -600,6 +600,18 @@ sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans) {
     });)
 }
 
+sts_status sts_jac_matvec_noalloc(sts_jac_t h, const double *x, double *y, int trans) {
+    STS_TRY(check_handle(h, x, y, "sts_jac_matvec_noalloc"));
+    if (h->rep != STS_REP_FACTORED)
+        return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_noalloc: needs the factored representation");
+    if (trans && !h->has_T)
+        return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_noalloc: trans = 1 needs enable_transpose");
+    const int dir = trans ? 1 : 0;
+    STS_GUARD(return with_layout<double>(h, x, y, h->vin, h->vout, [&](const double *a, double *b) {
+        return mv_apply64_noalloc(h, dir, a, b);
+    });)
+}
+
 sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans) {
     STS_TRY(check_handle(h, x, y, "sts_jac_matvec_f32"));
     if (h->dtype != STS_MIXED) return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_f32: handle has no FP32 operators");

@@ -12,6 +12,7 @@
 // same kernels on the transposed plan (S^T patterns, roles of u and v swapped).
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "ring.cuh"
@@ -424,6 +425,52 @@ sts_status mv_apply64(sts_jac_s *h, int dir, const double *x, double *y, double 
 sts_status mv_dots64(sts_jac_s *h, int dir, const double *x, double *c) {
     const MvPlan &P = h->mv[dir];
     return dots_launch<double>(h, make_args<double>(h, dir, P.main64, P.dotv64, x, nullptr, c));
+}
+
+// ---------------------------------------------------------------------------
+// Matvec without any device allocation: the pass-1 dot products go to a
+// library-owned, file-scope device array instead of a handle buffer.  The
+// array (kNoAllocScratch doubles, 4 MiB) exists on every GPU that loads the
+// library, for the life of the process.  Its device address is looked up with
+// cudaGetSymbolAddress once per device, on the first call made while that
+// device is current.  Every call shares the array, so calls that overlap on the
+// GPU (several streams, several threads) race on it; each call writes every
+// entry it later reads, so nothing has to be cleared between calls.
+constexpr size_t kNoAllocScratch = size_t(1) << 19;
+static __device__ __align__(256) double g_noalloc_dots[kNoAllocScratch];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+sts_status mv_apply64_noalloc(sts_jac_s *h, int dir, const double *x, double *y) {
+    const MvPlan &P = h->mv[dir];
+    const size_t need = (size_t)h->n_tiles * P.n_dtasks * kTile;
+    if (need > kNoAllocScratch)
+        return set_error(STS_ERR_INVALID_ARG,
+                         "sts_jac_matvec_noalloc: this Jacobian needs %zu scratch values (tiles x dot tasks x 32), "
+                         "more than the %zu of the static buffer; use sts_jac_matvec",
+                         need, kNoAllocScratch);
+    int dev = 0;
+    STS_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_noalloc: device %d out of range", dev);
+    double *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_dots);
+            if (e != cudaSuccess || !p)
+                return set_error(STS_ERR_CUDA, "sts_jac_matvec_noalloc: cudaGetSymbolAddress failed: %s",
+                                 cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double *>(p);
+        }
+        c = g_noalloc_ptr[dev];
+    }
+    return mv_launch<double>(h, make_args<double>(h, dir, P.main64, P.dotv64, x, y, c));
 }
 
 sts_status mv_apply32(sts_jac_s *h, int dir, const float *x, float *y, float *c) {

@@ -265,6 +265,7 @@ sts_status mv_repack(sts_jac_s *h, int dir, const double *S, const double *U, co
 sts_status mv_apply64(sts_jac_s *h, int dir, const double *x, double *y, double *c);
 sts_status mv_apply32(sts_jac_s *h, int dir, const float *x, float *y, float *c);
 sts_status mv_dots64(sts_jac_s *h, int dir, const double *x, double *c);   // pass 1 only
+sts_status mv_apply64_noalloc(sts_jac_s *h, int dir, const double *x, double *y);
 sts_status to_internal64(sts_jac_s *h, const double *x, double *xi);
 sts_status from_internal64(sts_jac_s *h, const double *xi, double *x);
 sts_status to_internal32(sts_jac_s *h, const float *x, float *xi);
