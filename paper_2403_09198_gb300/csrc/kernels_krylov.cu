@@ -65,13 +65,18 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long
     }
 }
 
-// out[i] = sum_b partial[b * ld + i], fixed order.
-__global__ void k_reduce(const double *partial, int nblk, int ld, int cnt, double *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// out[i] = sum_b partial[b * ld + i]: one block per output; thread t adds
+// partials t, t + 256, ... and a fixed tree adds the threads, so the order of
+// additions never depends on scheduling.
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const double *partial, int nblk, int ld, int cnt,
+                                                        double *out) {
+    __shared__ double sh[kRedThreads / 32];
+    const int i = blockIdx.x;
     if (i >= cnt) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * ld + i];
-    out[i] = s;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(size_t)b * ld + i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[i] = s;
 }
 
 // w -= sum_{i<k} h_i V_i; with norm = 1 also partial[blk] = sum w^2 after the update.
@@ -178,7 +183,7 @@ struct Red {
             k_mdot<<<kRedBlocks, kRedThreads, 0, h->stream>>>(V, n, i0, cnt, w, K.partial, ld, sf);
             STS_LAUNCHED();
         }
-        k_reduce<<<(k + (self ? 1 : 0) + 63) / 64, 64, 0, h->stream>>>(K.partial, kRedBlocks, ld, k + (self ? 1 : 0), out);
+        k_reduce<<<k + (self ? 1 : 0), kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, ld, k + (self ? 1 : 0), out);
         STS_LAUNCHED();
         return STS_OK;
     }
@@ -187,7 +192,7 @@ struct Red {
         k_update<<<kRedBlocks, kRedThreads, 0, h->stream>>>(w, V, n, hcoef, k, K.partial, norm);
         STS_LAUNCHED();
         if (norm) {
-            k_reduce<<<1, 64, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
+            k_reduce<<<1, kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
             STS_LAUNCHED();
         }
         return STS_OK;
@@ -196,7 +201,7 @@ struct Red {
         Krylov &K = h->kry;
         k_norm2<<<kRedBlocks, kRedThreads, 0, h->stream>>>(v, n, K.partial);
         STS_LAUNCHED();
-        k_reduce<<<1, 64, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
+        k_reduce<<<1, kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
         STS_LAUNCHED();
         return STS_OK;
     }

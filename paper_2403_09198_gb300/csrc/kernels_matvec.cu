@@ -45,9 +45,6 @@ struct MvArgs {
 template <typename T> struct Chunk { static constexpr int CH = 8; };
 template <> struct Chunk<float> { static constexpr int CH = 16; };
 
-// Shared-memory ring of the structured level rows: stages of kMvStage positions.
-constexpr int kMvStage = 8;
-constexpr int kMvStages = 4;
 
 // Pass 1: one warp per (tile, dot task); lane = cell.  A dot task is one
 // length-b dot product  c = d . x_j  with j the neighbour of the task's slot:
@@ -205,34 +202,55 @@ __global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
         for (int f = 0; f < NF; ++f) xf[s][f] = s < ns ? __ldg(xs[s] + (size_t)(N + f) * ncp) : T(0);
     }
     const int p0 = g * a.s_gl, p1 = min(N, p0 + a.s_gl);
-    // the group's rows are contiguous in the stream: stream them through this
-    // warp's shared-memory ring
+    // Rows are staged one per shared-memory stage, double-buffered: the copy
+    // of row p+1 is in flight while row p is multiplied, and every read of the
+    // staged row uses a compile-time offset.
+    constexpr int PIECES = kTile * (int)sizeof(T) / 16;       // 16-byte pieces per position
+    const int RL = a.s_rl;
+    const int npieces = RL * PIECES;
     extern __shared__ __align__(16) unsigned char mv_smem[];
-    T *ring_mem = reinterpret_cast<T *>(mv_smem) + (size_t)(threadIdx.x >> 5) * kMvStages * kMvStage * kTile;
-    Ring<T, kMvStage, kMvStages> R;
-    R.start(ring_mem, a.main + ((size_t)t * a.tile_len + (size_t)p0 * a.s_rl) * kTile, kTile,
-            (p1 - p0) * a.s_rl, lane);
+    T *stage0 = reinterpret_cast<T *>(mv_smem) + (size_t)(threadIdx.x >> 5) * 2 * RL * kTile;
+    const T *__restrict__ src0 = a.main + ((size_t)t * a.tile_len + (size_t)p0 * RL) * kTile;
+    auto issue = [&](int row, int stg) {
+        const T *src = src0 + (size_t)(row - p0) * RL * kTile;
+        T *dst = stage0 + (size_t)stg * RL * kTile;
+        for (int idx = lane; idx < npieces; idx += kTile) {
+            const int pos = idx / PIECES, piece = idx % PIECES;
+            cp_async16(dst + pos * kTile + piece * (16 / (int)sizeof(T)),
+                       src + (size_t)pos * kTile + piece * (16 / (int)sizeof(T)));
+        }
+        cp_async_commit();
+    };
+    issue(p0, 0);
     for (int p = p0; p < p1; ++p) {
+        if (p + 1 < p1) issue(p + 1, (p + 1 - p0) & 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const T *v = stage0 + (size_t)((p - p0) & 1) * RL * kTile + lane;
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k <= 2 * WD; ++k) {
             const int q = min(max(p - WD + k, 0), N - 1);    // clipped band entries carry zeros
-            acc = fma(R.next(), __ldg(xs[0] + (size_t)q * ncp), acc);
+            acc = fma(v[k * kTile], __ldg(xs[0] + (size_t)q * ncp), acc);
         }
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc = fma(R.next(), xf[0][f], acc);
+        for (int f = 0; f < NF; ++f) acc = fma(v[(2 * WD + 1 + f) * kTile], xf[0][f], acc);
 #pragma unroll
         for (int s = 1; s < NS; ++s) {
             if (s < ns) {
-                acc = fma(R.next(), __ldg(xs[s] + (size_t)p * ncp), acc);
+                const T *vs = v + (2 * WD + 1 + NF + (s - 1) * (1 + NF)) * kTile;
+                acc = fma(vs[0], __ldg(xs[s] + (size_t)p * ncp), acc);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) acc = fma(R.next(), xf[s][f], acc);
+                for (int f = 0; f < NF; ++f) acc = fma(vs[(1 + f) * kTile], xf[s][f], acc);
             }
         }
-        for (int k = 0; k < nps; ++k) acc = fma(R.next(), __ldg(cc + (size_t)k * kTile), acc);
+        const T *vu = v + (2 * WD + 1 + NF + (ns - 1) * (1 + NF)) * kTile;
+        for (int k = 0; k < nps; ++k) acc = fma(vu[k * kTile], __ldg(cc + (size_t)k * kTile), acc);
         a.y[(size_t)p * ncp + cell] = acc;
+        __syncwarp();     // the stage is refilled by the next iteration's copy
     }
-    R.finish();
+    cp_async_wait<0>();
 }
 
 // Repack the public values into one stream of one direction.  Each stream
@@ -378,7 +396,8 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
     const long long warps = (long long)a.n_tiles * a.n_groups;
     const unsigned grid = (unsigned)((warps + 3) / 4);
     if (a.structured) {
-        const size_t smem = (size_t)4 * kMvStages * kMvStage * kTile * sizeof(T);
+        constexpr int kWarpsPerBlock = 2;      // two row stages per warp; small blocks pack the SM finely
+        const size_t smem = (size_t)kWarpsPerBlock * 2 * a.s_rl * kTile * sizeof(T);
         void (*kern)(MvArgs<T>) = nullptr;
         switch (a.wd) {
             case 0: kern = k_mv_struct<T, 0>; break;
@@ -388,7 +407,7 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
             default: kern = k_mv_struct<T, 4>; break;
         }
         if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, 128, smem, h->stream>>>(a);
+        kern<<<(unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * kTile, smem, h->stream>>>(a);
     } else {
         k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);
     }
