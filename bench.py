@@ -122,6 +122,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_elapsed(elapsed: float, device) -> float:
+    """Max over ranks of a per-rank elapsed time; unchanged in a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -274,11 +285,7 @@ def run_ours(args):
         torch.distributed.barrier()
     launches = binding.launch_count() - l0
     ck = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = aggregate_elapsed(e0.elapsed_time(e1) / 1e3, dev)
     value = ops_done * ws / elapsed
     mv_ms = statistics.median(per["mv"])
     ap_ms = statistics.median(per["ap"])
@@ -420,6 +427,151 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _timer(stream):
+    import torch
+
+    def avg(fn, reps):
+        for _ in range(2):
+            fn()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        c.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(c) / reps
+    return avg
+
+
+def run_report(args):
+    """Extra measurements beyond the default line (one JSON line each):
+    nsweep  matvec time and handle memory vs N, factored vs dense, fitted exponents;
+    large   256x256, N=200: factored vs dense matvec, apply, setup, GMRES time to 1e-10;
+    mixed   512x512, N=60: FP64 GMRES vs FP32/FP64 flexible GMRES, error vs the oracle."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2403_09198_gb300 import inputs
+    from paper_2403_09198_gb300.binding import StsJacobian
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    avg = _timer(stream)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    if args.report == "nsweep":
+        for L in (40, 128):
+            rows = []
+            for N in (10, 20, 40, 60, 100, 150, 200):
+                if L == 128 and N > 100:
+                    continue            # dense 128x128 blocks above N=100 exceed a minute of setup
+                w = inputs.make_workload(L, L, N=N, w=2, r_diag=2, r_off=1, seed=N)
+                S, U, V = t(w.S), t(w.U), t(w.V)
+                x = torch.randn(w.n, dtype=torch.float64, device="cuda")
+                y = torch.empty_like(x)
+                f = StsJacobian(w, S, U, V, layout="component")
+                tf = avg(lambda: f.matvec(x, out=y), 20)
+                mf = f.memory_bytes()
+                f.close()
+                d = StsJacobian(w, S, U, V, layout="component", dense=True)
+                td = avg(lambda: d.matvec(x, out=y), 10)
+                md = d.memory_bytes()
+                d.close()
+                rows.append(dict(N=N, b=w.b, factored_ms=tf, dense_ms=td, factored_bytes=mf, dense_bytes=md,
+                                 S_values=int(w.S.shape[0])))
+                del S, U, V
+                torch.cuda.empty_cache()
+            Ns = np.log([r["b"] for r in rows])
+            fit = lambda key: float(np.polyfit(Ns, np.log([r[key] for r in rows]), 1)[0])
+            print(json.dumps({"report": "nsweep", "grid": f"{L}x{L}", "rows": rows,
+                              "slope_vs_b": {k: fit(k) for k in ("factored_ms", "dense_ms", "factored_bytes",
+                                                                 "dense_bytes")}}), flush=True)
+        return
+
+    if args.report == "large":
+        w = inputs.named_workload("grid256_N200")
+        S, U, V, b = t(w.S), t(w.U), t(w.V), t(w.rhs)
+        x = torch.randn(w.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        out = {"report": "large", "workload": "grid256_N200: 256x256 cells, N=200, b=203, band +-4, 3/1 pairs"}
+        for name, kw in (("factored", {}), ("dense", {"dense": True})):
+            j = StsJacobian(w, S, U, V, layout="component", **kw)
+            r = {"matvec_ms": avg(lambda: j.matvec(x, out=y), 5 if kw else 20),
+                 "memory_GB": j.memory_bytes() / 1e9}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            j.bjacobi_setup()
+            r["setup_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["apply_ms"] = avg(lambda: j.bjacobi_apply(x, out=y), 5 if kw else 20)
+            j.gmres(b, rtol=1e-10, restart=30)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = j.gmres(b, rtol=1e-10, restart=30)
+            r["gmres_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["gmres_iterations"] = info.iterations
+            r["gmres_true_rel_residual"] = info.true_rel_residual
+            out[name] = r
+            j.close()
+            torch.cuda.empty_cache()
+        out["speedup"] = {k: out["dense"][k] / out["factored"][k] for k in ("matvec_ms", "apply_ms", "setup_ms",
+                                                                             "gmres_ms")}
+        print(json.dumps(out), flush=True)
+        return
+
+    if args.report == "mixed":
+        import oracle
+        oracle.build()
+        w = inputs.named_workload("grid512_N60")
+        S, U, V, b = t(w.S), t(w.U), t(w.V), t(w.rhs)
+        j = StsJacobian(w, S, U, V, mixed=True)
+        j.bjacobi_setup()
+        res = {"report": "mixed", "workload": "grid512_N60: 512x512 cells, N=60, b=63, 2/1 pairs"}
+        for mode in ("fp64", "mixed"):
+            j.gmres(b, rtol=1e-10, restart=30, mixed=(mode == "mixed"))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xs, info = j.gmres(b, rtol=1e-10, restart=30, mixed=(mode == "mixed"))
+            res[mode] = {"ms": 1e3 * (time.perf_counter() - t0), "iterations": info.iterations,
+                         "restarts": info.restarts, "true_rel_residual": info.true_rel_residual,
+                         "x": xs.cpu().numpy()}
+        x32 = torch.randn(w.n, dtype=torch.float32, device="cuda")
+        res["fp32_matvec_ms"] = avg(lambda: j.matvec(x32, out=torch.empty_like(x32)), 20)
+        res["fp32_apply_ms"] = avg(lambda: j.bjacobi_apply(x32, out=torch.empty_like(x32)), 20)
+        x64 = x32.double()
+        res["fp64_matvec_ms"] = avg(lambda: j.matvec(x64, out=torch.empty_like(x64)), 20)
+        res["fp64_apply_ms"] = avg(lambda: j.bjacobi_apply(x64, out=torch.empty_like(x64)), 20)
+        j.close()
+        # the FP64 oracle solves the same system on the host cores
+        J = oracle.Jacobian.from_workload(w)
+        t0 = time.perf_counter()
+        xo, io = oracle.gmres(J, w.rhs, restart=30, rtol=1e-12)
+        res["oracle"] = {"s": time.perf_counter() - t0, "iterations": io["iterations"],
+                         "true_rel_residual": io["true_rel"], "cores": oracle.max_threads()}
+        for mode in ("fp64", "mixed"):
+            xm = res[mode].pop("x")
+            res[mode]["rel_error_vs_oracle"] = float(np.linalg.norm(xm - xo) / np.linalg.norm(xo))
+        # kappa estimate of J: power iterations on J^T J and on (J^T J)^-1 via the oracle
+        rng = np.random.default_rng(0)
+        v = rng.standard_normal(w.n)
+        for _ in range(8):
+            v = oracle.matvec(J, oracle.matvec(J, v), trans=True)
+            v /= np.linalg.norm(v)
+        smax = np.sqrt(np.linalg.norm(oracle.matvec(J, oracle.matvec(J, v), trans=True)))
+        u = rng.standard_normal(w.n)
+        F = oracle.bj_setup(J)
+        for _ in range(4):
+            u, _ = oracle.gmres(J, u, restart=30, rtol=1e-12, factors=F)
+            u, _ = oracle.gmres(J, u, restart=30, rtol=1e-12, trans=True, factors=F)
+            u /= np.linalg.norm(u)
+        z, _ = oracle.gmres(J, u, restart=30, rtol=1e-12, factors=F)
+        z, _ = oracle.gmres(J, z, restart=30, rtol=1e-12, trans=True, factors=F)
+        smin = 1.0 / np.sqrt(np.linalg.norm(z))
+        res["kappa_estimate"] = float(smax / smin)
+        res["bound_kappa_x_1e-10"] = res["kappa_estimate"] * 1e-10
+        print(json.dumps(res), flush=True)
+        return
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -431,8 +583,12 @@ def main():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--report", choices=["nsweep", "large", "mixed"], default=None,
+                   help="print an extra measurement instead of the benchmark line")
     args = p.parse_args()
-    if args.impl == "reference":
+    if args.report:
+        run_report(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

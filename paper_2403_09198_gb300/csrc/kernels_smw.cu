@@ -302,26 +302,35 @@ struct SApplyArgs {
     const double *Cinv;     // [r][r][ncp]
     const T *x;
     T *y;
-    int len, b, N, r, ncp, trans;
+    int len, b, N, r, ncp, trans, n_tiles;
 };
 
+constexpr int kApWarps = 4;     // warps per block of the structured apply (one per sub-partition)
+constexpr int kSApStages = 4;   // ring stages of the structured apply
+
+// One block of kApWarps warps per SM; warp w of block k takes tiles
+// w * gridDim.x + k, + kApWarps * gridDim.x, ...  so that tiles are dealt to
+// SMs round-robin and no sub-partition runs two tiles while another idles.
 template <typename T, int W, int RMAX>
-__global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
+__global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
     constexpr int NF = kStructNF;
+    constexpr int FW = W + NF;                      // forward row width
+    constexpr int BW = 1 + NF + W + RMAX;           // backward row width
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
-    T *ws = stg + kApStages * kApStage * kTile;                 // [b][32]: w, then x0
-    const int lane = threadIdx.x;
-    const int tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5;
+    T *stg = reinterpret_cast<T *>(smem_raw) + (size_t)warp * (kSApStages * kApStage + a.b) * kTile;
+    T *ws = stg + kSApStages * kApStage * kTile;                // [b][32]: w, then x0
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    for (int tile = warp * gridDim.x + blockIdx.x; tile < a.n_tiles; tile += nwarps * gridDim.x) {
     const int cell = tile * kTile + lane;
     const size_t P = a.ncp;
     const int N = a.N, r = a.r;
-    Ring<T, kApStage, kApStages> R;
+    Ring<T, kApStage, kSApStages> R;
     R.start(stg, a.st + (size_t)tile * kTile, P, a.len, lane);
     const T *__restrict__ x = a.x;
     for (int i = 0; i < a.b; ++i) ws[i * kTile + lane] = __ldg(x + i * P + cell);
-    auto next = [&]() -> T { return R.next(); };
-    // forward sweep
+    // forward sweep: row i = [W band coefficients, oldest first | NF flow-row coefficients]
     T win[W > 0 ? W : 1];
 #pragma unroll
     for (int k = 0; k < W; ++k) win[k] = T(0);
@@ -329,63 +338,65 @@ __global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) accf[f] = T(0);
     for (int i = 0; i < N; ++i) {
+        const T *v = R.take(FW);
         T acc = ws[i * kTile + lane];
 #pragma unroll
-        for (int k = 0; k < W; ++k) acc = fma(-next(), win[k], acc);
+        for (int k = 0; k < W; ++k) acc = fma(-v[k * kTile], win[k], acc);
         ws[i * kTile + lane] = acc;
 #pragma unroll
         for (int k = 0; k + 1 < W; ++k) win[k] = win[k + 1];
         if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) accf[f] = fma(next(), acc, accf[f]);
+        for (int f = 0; f < NF; ++f) accf[f] = fma(v[(W + f) * kTile], acc, accf[f]);
     }
     T wf[NF];
-    wf[0] = ws[N * kTile + lane] - accf[0];
-    wf[1] = fma(-next(), wf[0], ws[(N + 1) * kTile + lane] - accf[1]);
     {
-        const T c0 = next(), c1 = next();
-        wf[2] = fma(-c1, wf[1], fma(-c0, wf[0], ws[(N + 2) * kTile + lane] - accf[2]));
+        const T *v = R.take(3);                                 // (N+1,N), (N+2,N), (N+2,N+1)
+        wf[0] = ws[N * kTile + lane] - accf[0];
+        wf[1] = fma(-v[0], wf[0], ws[(N + 1) * kTile + lane] - accf[1]);
+        wf[2] = fma(-v[2 * kTile], wf[1], fma(-v[kTile], wf[0], ws[(N + 2) * kTile + lane] - accf[2]));
     }
     // backward sweep with t = V^T x0 accumulated on the way
     T t[RMAX];
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) t[k] = T(0);
     T xf[NF];
-    xf[2] = next() * wf[2];
+    {
+        // [d2, V(N+2) | d1, u(N+1,N+2), V(N+1) | d0, u(N,N+1), u(N,N+2), V(N)], V padded to RMAX
+        const T *v = R.take(6 + 3 * RMAX);
+        xf[2] = v[0] * wf[2];
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k)
-        if (k < r) t[k] = fma(next(), xf[2], t[k]);
-    xf[1] = next() * wf[1];
-    xf[1] = fma(-next(), xf[2], xf[1]);
+        for (int k = 0; k < RMAX; ++k) t[k] = fma(v[(1 + k) * kTile], xf[2], t[k]);
+        const T *v1 = v + (1 + RMAX) * kTile;
+        xf[1] = fma(-v1[kTile], xf[2], v1[0] * wf[1]);
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k)
-        if (k < r) t[k] = fma(next(), xf[1], t[k]);
-    xf[0] = next() * wf[0];
-    xf[0] = fma(-next(), xf[1], xf[0]);
-    xf[0] = fma(-next(), xf[2], xf[0]);
+        for (int k = 0; k < RMAX; ++k) t[k] = fma(v1[(2 + k) * kTile], xf[1], t[k]);
+        const T *v0 = v1 + (2 + RMAX) * kTile;
+        xf[0] = fma(-v0[2 * kTile], xf[2], fma(-v0[kTile], xf[1], v0[0] * wf[0]));
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k)
-        if (k < r) t[k] = fma(next(), xf[0], t[k]);
+        for (int k = 0; k < RMAX; ++k) t[k] = fma(v0[(3 + k) * kTile], xf[0], t[k]);
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) ws[(N + f) * kTile + lane] = xf[f];
+    // backward row i = [pivot inverse | NF flow | W band, farthest first | V entries (RMAX)]
     T xw[W > 0 ? W : 1];
 #pragma unroll
     for (int k = 0; k < W; ++k) xw[k] = T(0);
     for (int i = N - 1; i >= 0; --i) {
-        T acc = next() * ws[i * kTile + lane];
+        const T *v = R.take(BW);
+        T acc = v[0] * ws[i * kTile + lane];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc = fma(-next(), xf[f], acc);
+        for (int f = 0; f < NF; ++f) acc = fma(-v[(1 + f) * kTile], xf[f], acc);
 #pragma unroll
-        for (int k = W - 1; k >= 0; --k) acc = fma(-next(), xw[k], acc);
+        for (int k = 0; k < W; ++k) acc = fma(-v[(1 + NF + k) * kTile], xw[W - 1 - k], acc);
         ws[i * kTile + lane] = acc;
 #pragma unroll
         for (int k = W - 1; k > 0; --k) xw[k] = xw[k - 1];
         if (W > 0) xw[0] = acc;
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k)
-            if (k < r) t[k] = fma(next(), acc, t[k]);
+        for (int k = 0; k < RMAX; ++k) t[k] = fma(v[(1 + NF + W + k) * kTile], acc, t[k]);
     }
-    // z = C^-1 t in FP64, then x = x0 - W z
+    // z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q])
     T z[RMAX];
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) {
@@ -402,13 +413,15 @@ __global__ void __launch_bounds__(32) k_smw_sapply(SApplyArgs<T> a) {
         z[k] = (T)sacc;
     }
     for (int q = 0; q < a.b; ++q) {
-        T v = ws[q * kTile + lane];
+        const T *v = R.take(RMAX);
+        T val = ws[q * kTile + lane];
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k)
-            if (k < r) v = fma(-next(), z[k], v);
-        a.y[q * P + cell] = v;
+        for (int k = 0; k < RMAX; ++k) val = fma(-v[k * kTile], z[k], val);
+        a.y[q * P + cell] = val;
     }
     R.finish();
+    __syncwarp();
+    }
 }
 
 // Structured stream packing: per position a source code and argument
@@ -607,9 +620,23 @@ sts_status smw_build(sts_jac_s *h) {
         const int NF = kStructNF, N = b - NF, r = h->r_diag;
         M.s_w = sw;
         auto sl = [&](int i, int j) { return slot[(size_t)i * b + j]; };
+        const int RMAX = r <= 2 ? 2 : 4;       // must match the kernel instance chosen at apply time
         for (int dir = 0; dir < 2; ++dir) {
-            std::vector<int> src, arg;
-            auto put = [&](int s_, int a_) { src.push_back(s_); arg.push_back(a_); };
+            std::vector<int> src, arg, rsrc, rarg;
+            auto put = [&](int s_, int a_) { rsrc.push_back(s_); rarg.push_back(a_); };
+            // close one row: rows never straddle a kApStage chunk (zero padding)
+            auto row = [&]() {
+                const int width = (int)rsrc.size(), off = (int)(src.size() % kApStage);
+                if (off + width > kApStage)
+                    for (int k = off; k < kApStage; ++k) { src.push_back(-4); arg.push_back(0); }
+                src.insert(src.end(), rsrc.begin(), rsrc.end());
+                arg.insert(arg.end(), rarg.begin(), rarg.end());
+                rsrc.clear();
+                rarg.clear();
+            };
+            auto vd = [&](int q) {                  // dot-vector entries of unknown q, padded to RMAX
+                for (int k = 0; k < RMAX; ++k) put(k < r ? -2 : -4, k < r ? k * b + q : 0);
+            };
             // lower factor of this direction: dir 0 L, dir 1 U'^T (U scaled by the row pivot inverse)
             auto lo = [&](int i, int j) {           // coefficient (i, j), i > j
                 if (dir == 0) put(sl(i, j), -1);
@@ -627,19 +654,22 @@ sts_status smw_build(sts_jac_s *h) {
                     else put(-4, 0);
                 }
                 for (int f = 0; f < NF; ++f) lo(N + f, i);
+                row();
             }
             lo(N + 1, N);
             lo(N + 2, N);
             lo(N + 2, N + 1);
+            row();
             put(-1, N + 2);
-            for (int k = 0; k < r; ++k) put(-2, k * b + N + 2);
+            vd(N + 2);
             put(-1, N + 1);
             up(N + 1, N + 2);
-            for (int k = 0; k < r; ++k) put(-2, k * b + N + 1);
+            vd(N + 1);
             put(-1, N);
             up(N, N + 1);
             up(N, N + 2);
-            for (int k = 0; k < r; ++k) put(-2, k * b + N);
+            vd(N);
+            row();
             for (int i = N - 1; i >= 0; --i) {
                 put(-1, i);
                 for (int f = 0; f < NF; ++f) up(i, N + f);
@@ -648,10 +678,13 @@ sts_status smw_build(sts_jac_s *h) {
                     if (j < N) up(i, j);
                     else put(-4, 0);
                 }
-                for (int k = 0; k < r; ++k) put(-2, k * b + i);
+                vd(i);
+                row();
             }
-            for (int q = 0; q < b; ++q)
-                for (int k = 0; k < r; ++k) put(-3, k * b + q);
+            for (int q = 0; q < b; ++q) {
+                for (int k = 0; k < RMAX; ++k) put(k < r ? -3 : -4, k < r ? k * b + q : 0);
+                row();
+            }
             for (size_t e = 0; e < src.size(); ++e)
                 if (src[e] < -4 || (src[e] >= 0 && src[e] >= M.nnz_lu))
                     return set_error(STS_ERR_INVALID_ARG, "internal: structured apply table");
@@ -798,7 +831,12 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     SApplyArgs<T> a;
     a.st = st; a.Cinv = M.Cinv; a.x = x; a.y = z;
     a.len = M.s_len; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp; a.trans = dir;
-    const size_t smem = ((size_t)kApStages * kApStage + h->b) * kTile * sizeof(T);
+    a.n_tiles = h->n_tiles;
+    const size_t per_warp = ((size_t)kSApStages * kApStage + h->b) * kTile * sizeof(T);
+    const int wpb = (int)std::min<size_t>(kApWarps, (size_t)(227 * 1024) / per_warp);
+    if (wpb < 1)
+        return set_error(STS_ERR_INVALID_ARG, "block size %d needs %zu bytes of shared memory per warp", h->b, per_warp);
+    const size_t smem = (size_t)wpb * per_warp;
     void (*kern)(SApplyArgs<T>) = nullptr;
     const bool r2 = a.r <= 2;
     switch (M.s_w) {
@@ -809,7 +847,11 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
         default: kern = r2 ? k_smw_sapply<T, 4, 2> : k_smw_sapply<T, 4, 4>; break;
     }
     if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<h->n_tiles, kTile, smem, h->stream>>>(a);
+    int dev = 0, nsm = 0;
+    STS_CK(cudaGetDevice(&dev));
+    STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::max(1, std::min(nsm, h->n_tiles));
+    kern<<<blocks, wpb * kTile, smem, h->stream>>>(a);
     STS_LAUNCHED();
     return STS_OK;
 }

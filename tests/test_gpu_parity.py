@@ -217,6 +217,41 @@ def test_gmres_not_converged_keeps_x():
     jac.close()
 
 
+def test_gmres_nan_is_reported():
+    """NaN in the right-hand side or in the Jacobian values ends the solve with
+    STS_ERR_NUMERIC instead of returning garbage."""
+    w = workload("ragged5x3")
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    rhs = w.rhs.copy()
+    rhs[5] = np.nan
+    with pytest.raises(StsError) as e:
+        jac.gmres(dev(rhs))
+    assert e.value.status == 6
+    U = w.U.copy()
+    U[3, 1] = np.nan
+    jac.update_values(dev(w.S), dev(U), dev(w.V))
+    with pytest.raises(StsError) as e:
+        jac.bjacobi_setup()
+        jac.gmres(dev(w.rhs))
+    assert e.value.status in (4, 6)
+    jac.close()
+
+
+def test_values_from_host_memory():
+    """Values handed over in host memory (values_on_host = 1) give the same operator."""
+    w = workload("grid16_N10")
+    J = oracle_jac(w)
+    jac = StsJacobian(w, w.S, w.U, w.V, transpose=True)       # numpy arrays: host path
+    x = np.random.default_rng(9).standard_normal(w.n)
+    for trans in (False, True):
+        assert rel_err(host(jac.matvec(dev(x), trans=trans)), oracle.matvec(J, x, trans=trans)) <= TOL64
+    jac.update_values(w.S * 2.0, w.U, w.V)
+    J2 = oracle_jac(w, S=w.S * 2.0)
+    assert rel_err(host(jac.matvec(dev(x))), oracle.matvec(J2, x)) <= TOL64
+    jac.close()
+
+
 def test_gmres_zero_rhs():
     w = workload("ragged5x3")
     jac = _jac(w)
