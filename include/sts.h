@@ -56,7 +56,7 @@ enum {
     STS_ERR_SINGULAR = 4,      /* zero pivot in S_ii or singular capacitance C_k        */
     STS_ERR_NOT_CONVERGED = 5, /* GMRES hit max_iters; the returned x is still valid    */
     STS_ERR_NUMERIC = 6,       /* NaN or Inf met in a residual or Krylov quantity       */
-    STS_ERR_TIMEOUT = 7,       /* reserved for bounded device-side waits                */
+    STS_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up (see bjacobi_apply) */
     STS_ERR_NOT_SETUP = 8      /* block-Jacobi used before sts_jac_bjacobi_setup        */
 };
 
@@ -208,7 +208,8 @@ sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans);
  * W_k = S_ii^-1 U_k, C_k = I + V_k^T W_k (FP64) and C_k^-1.  Dense-BSR
  * representation: per-cell dense LU with partial pivoting.  Synchronous.
  * Errors: STS_ERR_SINGULAR when a pivot fails |p| > 1e-14 * max|row of S_ii|, or
- * C_k is singular; the message names the first failing cell.
+ * C_k is singular; the message names the first failing cell.  STS_ERR_TIMEOUT
+ * when an apply since the last check reported a timed-out wait (see below).
  */
 sts_status sts_jac_bjacobi_setup(sts_jac_t h);
 
@@ -217,6 +218,10 @@ sts_status sts_jac_bjacobi_setup(sts_jac_t h);
  * x0 = S_ii^-1 x_i, t = V^T x0, z_i = x0 - W C^-1 t (Section 6 SMW-1..3, with the
  * minus sign the Woodbury identity requires).  FP64 device vectors; x and z
  * must not overlap.  Errors: STS_ERR_NOT_SETUP.  Asynchronous.
+ * The structured-pattern kernel streams its coefficients through shared memory
+ * with bulk copies and waits for each at most about one second; a wait that
+ * gives up leaves z invalid and sets a flag on the handle that the next
+ * sts_gmres_solve or sts_jac_bjacobi_setup reports as STS_ERR_TIMEOUT.
  */
 sts_status sts_jac_bjacobi_apply(sts_jac_t h, const double *x, double *z, int trans);
 
@@ -231,7 +236,8 @@ sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int 
  * Mixed mode: FP32 matvec and block-Jacobi, FP64 Krylov basis, Arnoldi,
  * residual refresh and capacitance solves, flexible GMRES.  Convergence is
  * declared on the FP64 true residual only.  Synchronous; info may be NULL.
- * Errors: STS_ERR_NOT_CONVERGED (x valid), STS_ERR_NUMERIC, STS_ERR_NOT_SETUP.
+ * Errors: STS_ERR_NOT_CONVERGED (x valid), STS_ERR_NUMERIC, STS_ERR_NOT_SETUP,
+ * STS_ERR_TIMEOUT (see sts_jac_bjacobi_apply).
  */
 sts_status sts_gmres_solve(sts_jac_t h, const double *b, double *x, const sts_gmres_opts *opts,
                            sts_gmres_info *info);

@@ -240,7 +240,7 @@ sts_status build_plan(sts_jac_s *h, int dir, bool with_streams) {
         P.s_wd = wd;
         P.sN = N;
         P.s_rl = (2 * wd + 1 + NF) + (n_slots - 1) * (1 + NF) + P.n_pslots;
-        P.s_gl = std::max(1, (180 + P.s_rl / 2) / P.s_rl);
+        P.s_gl = std::max(1, (180 + P.s_rl / 2) / P.s_rl);    // about 180 FMAs per lane and warp item
         P.n_lgroups = (N + P.s_gl - 1) / P.s_gl;
         P.n_groups = P.n_lgroups + 1;
         P.tile_len = (long long)pos_kind.size();
@@ -508,6 +508,11 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
         const size_t n = (size_t)b * h->ncp;
         if ((st = dalloc(h, &h->vin, n)) != STS_OK) break;
         if ((st = dalloc(h, &h->vout, n)) != STS_OK) break;
+        if ((st = dalloc(h, &h->d_err, 1)) != STS_OK) break;
+        if (cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) {
+            st = set_error(STS_ERR_CUDA, "sts_jac_create: cudaMemsetAsync failed");
+            break;
+        }
         const int nps = std::max(h->mv[0].n_dtasks, h->mv[1].n_dtasks);
         if ((st = dalloc(h, &h->c64, (size_t)h->n_tiles * nps * kTile + 1)) != STS_OK) break;
         if (h->dtype == STS_MIXED) {
@@ -558,6 +563,20 @@ sts_status check_handle(sts_jac_t h, const void *a, const void *b, const char *f
 }
 
 }  // namespace
+
+// A bounded device wait (bulk copies into shared memory) gave up since the
+// last check: report it once and clear the flag.
+sts_status check_device(sts_jac_s *h) {
+    if (!h->d_err) return STS_OK;
+    int flag = 0;
+    STS_CK(cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    STS_CK(cudaStreamSynchronize(h->stream));
+    if (!flag) return STS_OK;
+    STS_CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    return set_error(STS_ERR_TIMEOUT, "a shared-memory bulk copy did not complete within its time limit; results "
+                                      "of the matvecs and applies since the last check are invalid");
+}
+
 }  // namespace sts
 
 using namespace sts;
@@ -624,7 +643,8 @@ sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans) 
 
 sts_status sts_jac_bjacobi_setup(sts_jac_t h) {
     if (!h) return set_error(STS_ERR_INVALID_ARG, "sts_jac_bjacobi_setup: handle is NULL");
-    STS_GUARD(return h->rep == STS_REP_FACTORED ? smw_setup(h) : dense_setup(h);)
+    STS_GUARD(STS_TRY(check_device(h));
+              return h->rep == STS_REP_FACTORED ? smw_setup(h) : dense_setup(h);)
 }
 
 sts_status sts_jac_bjacobi_apply(sts_jac_t h, const double *x, double *z, int trans) {
@@ -653,7 +673,9 @@ sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int 
 sts_status sts_gmres_solve(sts_jac_t h, const double *b, double *x, const sts_gmres_opts *opts,
                            sts_gmres_info *info) {
     STS_TRY(check_handle(h, b, x, "sts_gmres_solve"));
-    STS_GUARD(return gmres(h, b, x, opts, info);)
+    STS_GUARD(const sts_status st = gmres(h, b, x, opts, info);
+              if (st == STS_OK || st == STS_ERR_NOT_CONVERGED || st == STS_ERR_NUMERIC) STS_TRY(check_device(h));
+              return st;)
 }
 
 sts_status sts_jac_grad(sts_jac_t h, const double *lambda, const double *x, double *gS, double *gU, double *gV) {

@@ -28,6 +28,7 @@ struct MvArgs {
     const T *x;             // [b][ncp]
     T *y;                   // [b][ncp]
     T *c;                   // [n_tiles][n_dtasks][32]
+    int *err;               // set when a bounded wait gave up
     const int *nbr;         // [n_tiles][n_slots][32]
     const unsigned *slot_mask;
     const int *grp_rows;
@@ -163,24 +164,51 @@ __global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
 // with x came out of pass 1:
 //   level row p: diagonal-slot band q = p-WD..p+WD and the NF flow columns,
 //                every neighbour slot's entry q = p and its flow columns, then
-//                the pair terms u_k[p] c_k.  The flow-column x values of every
-//                slot stay in registers for the whole group.
+//                the pair terms u_k[p] c_k.
 //   flow row N+f: sum over slots of the pass-1 flow dots, then the pair terms.
-template <typename T, int WD>
-__global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
+// Held in registers for the whole group: the flow-column x values of every
+// slot, the pass-1 pair dots c_k (when there are at most kStructRegPairs), and
+// a sliding window of the 2 WD + 1 own-cell x values of the band; the x values
+// of the next row are loaded one row ahead.  Each row's coefficients (s_rl
+// positions, contiguous) are staged in shared memory by one bulk copy, two
+// rows per warp in flight.
+constexpr int kStructRegPairs = 8;
+
+__host__ __device__ inline size_t mv_struct_warp_bytes(int rl, int elem) {
+    return 128 + 2 * (size_t)rl * kTile * elem;     // two mbarriers (padded), two row stages
+}
+
+template <typename T, int WD, bool CREG>
+__global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
     constexpr int NF = kStructNF;
     constexpr int NS = kStructMaxSlots;
+    constexpr int BANDW = 2 * WD + 1;
     const int lane = threadIdx.x & 31;
-    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (wid >= (long long)a.n_tiles * a.n_groups) return;
-    const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
     const int ns = a.n_slots, nps = a.n_pslots, N = a.sN;
     const size_t ncp = a.ncp;
+    const int RL = a.s_rl;
+    const uint32_t row_bytes = (uint32_t)RL * kTile * (uint32_t)sizeof(T);
+    extern __shared__ __align__(128) unsigned char mv_smem[];
+    unsigned char *mine = mv_smem + (size_t)(threadIdx.x >> 5) * mv_struct_warp_bytes(RL, (int)sizeof(T));
+    const uint32_t bar = smem_addr(mine);
+    T *stage0 = reinterpret_cast<T *>(mine + 128);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 8, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    uint32_t parity = 0;        // bit sg: parity of the next phase of stage sg to wait for
+    // persistent: warp items (tile, group) are dealt round-robin over the grid
+    const long long n_items = (long long)a.n_tiles * a.n_groups;
+    const long long wstep = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wid < n_items;
+         wid += wstep) {
+    const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
     const size_t cell = (size_t)t * kTile + lane;
     const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
-    const T *__restrict__ tile_stream = a.main + (size_t)t * a.tile_len * kTile + lane;
     if (g == a.n_lgroups) {
-        const T *__restrict__ su = tile_stream + (size_t)N * a.s_rl * kTile;
+        const T *__restrict__ su = a.main + ((size_t)t * a.tile_len + (size_t)N * RL) * kTile + lane;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             T acc = T(0);
@@ -189,8 +217,20 @@ __global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
                 acc = fma(__ldg(su + (size_t)(f * nps + k) * kTile), __ldg(cc + (size_t)k * kTile), acc);
             a.y[(size_t)(N + f) * ncp + cell] = acc;
         }
-        return;
+        continue;
     }
+    const int p0 = g * a.s_gl, p1 = min(N, p0 + a.s_gl);
+    const T *__restrict__ src0 = a.main + ((size_t)t * a.tile_len + (size_t)p0 * RL) * kTile;
+    auto issue = [&](int row) {             // bulk copy of one row into stage (row - p0) & 1
+        const int sg = (row - p0) & 1;
+        if (lane == 0) {
+            mbar_expect_tx(bar + 8u * sg, row_bytes);
+            bulk_copy_g2s(smem_addr(stage0 + (size_t)sg * RL * kTile), src0 + (size_t)(row - p0) * RL * kTile,
+                          row_bytes, bar + 8u * sg);
+        }
+    };
+    issue(p0);
+    if (p0 + 1 < p1) issue(p0 + 1);
     const T *xs[NS];
     T xf[NS][NF];
 #pragma unroll
@@ -201,56 +241,90 @@ __global__ void __launch_bounds__(128) k_mv_struct(MvArgs<T> a) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) xf[s][f] = s < ns ? __ldg(xs[s] + (size_t)(N + f) * ncp) : T(0);
     }
-    const int p0 = g * a.s_gl, p1 = min(N, p0 + a.s_gl);
-    // Rows are staged one per shared-memory stage, double-buffered: the copy
-    // of row p+1 is in flight while row p is multiplied, and every read of the
-    // staged row uses a compile-time offset.
-    constexpr int PIECES = kTile * (int)sizeof(T) / 16;       // 16-byte pieces per position
-    const int RL = a.s_rl;
-    const int npieces = RL * PIECES;
-    extern __shared__ __align__(16) unsigned char mv_smem[];
-    T *stage0 = reinterpret_cast<T *>(mv_smem) + (size_t)(threadIdx.x >> 5) * 2 * RL * kTile;
-    const T *__restrict__ src0 = a.main + ((size_t)t * a.tile_len + (size_t)p0 * RL) * kTile;
-    auto issue = [&](int row, int stg) {
-        const T *src = src0 + (size_t)(row - p0) * RL * kTile;
-        T *dst = stage0 + (size_t)stg * RL * kTile;
-        for (int idx = lane; idx < npieces; idx += kTile) {
-            const int pos = idx / PIECES, piece = idx % PIECES;
-            cp_async16(dst + pos * kTile + piece * (16 / (int)sizeof(T)),
-                       src + (size_t)pos * kTile + piece * (16 / (int)sizeof(T)));
-        }
-        cp_async_commit();
-    };
-    issue(p0, 0);
+    // pair dots in registers, aligned to the end: term k sits in slot poff + k, so
+    // a jump to case poff runs exactly the nps terms in order (no idle FMA slots)
+    const int poff = CREG ? kStructRegPairs - nps : 0;
+    T cq[CREG ? kStructRegPairs : 1];
+#pragma unroll
+    for (int i = 0; i < (CREG ? kStructRegPairs : 0); ++i)
+        cq[i] = i >= poff ? __ldg(cc + (size_t)(i - poff) * kTile) : T(0);
+    // band window: xb[k] = x_own[p - WD + k] (clipped; clipped entries carry zero coefficients)
+    T xb[BANDW];
+#pragma unroll
+    for (int k = 0; k + 1 < BANDW; ++k) xb[k + 1] = __ldg(xs[0] + (size_t)min(max(p0 - WD + k, 0), N - 1) * ncp);
+    T xbn = __ldg(xs[0] + (size_t)min(p0 + WD, N - 1) * ncp);
+    T xn[NS];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) xn[s] = s < ns ? __ldg(xs[s] + (size_t)p0 * ncp) : T(0);
+    T *yp = a.y + (size_t)p0 * ncp + cell;
+    T ylag = T(0);          // row p-1's result, stored during row p (its FMA has long completed)
     for (int p = p0; p < p1; ++p) {
-        if (p + 1 < p1) issue(p + 1, (p + 1 - p0) & 1);
-        else cp_async_commit();
-        cp_async_wait<1>();
-        __syncwarp();
-        const T *v = stage0 + (size_t)((p - p0) & 1) * RL * kTile + lane;
+        const int sg = (p - p0) & 1;
+        if (!mbar_wait_bounded(bar + 8u * sg, (parity >> sg) & 1u)) {
+            if (lane == 0) atomicExch(a.err, 1);
+            for (int q = p; q < min(p + 2, p1); ++q) {            // copies still in flight
+                const int sq = (q - p0) & 1;
+                if (!mbar_wait_bounded(bar + 8u * sq, (parity >> sq) & 1u)) break;
+                parity ^= 1u << sq;
+            }
+            return;
+        }
+        parity ^= 1u << sg;
+#pragma unroll
+        for (int k = 0; k + 1 < BANDW; ++k) xb[k] = xb[k + 1];
+        xb[BANDW - 1] = xbn;
+        T xc[NS];
+#pragma unroll
+        for (int s = 1; s < NS; ++s) xc[s] = xn[s];
+        if (p + 1 < p1) {
+            xbn = __ldg(xs[0] + (size_t)min(p + 1 + WD, N - 1) * ncp);
+#pragma unroll
+            for (int s = 1; s < NS; ++s)
+                if (s < ns) xn[s] = __ldg(xs[s] + (size_t)(p + 1) * ncp);
+        }
+        const T *v = stage0 + (size_t)sg * RL * kTile + lane;
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k <= 2 * WD; ++k) {
-            const int q = min(max(p - WD + k, 0), N - 1);    // clipped band entries carry zeros
-            acc = fma(v[k * kTile], __ldg(xs[0] + (size_t)q * ncp), acc);
-        }
+        for (int k = 0; k < BANDW; ++k) acc = fma(v[k * kTile], xb[k], acc);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) acc = fma(v[(2 * WD + 1 + f) * kTile], xf[0][f], acc);
+        for (int f = 0; f < NF; ++f) acc = fma(v[(BANDW + f) * kTile], xf[0][f], acc);
 #pragma unroll
         for (int s = 1; s < NS; ++s) {
             if (s < ns) {
-                const T *vs = v + (2 * WD + 1 + NF + (s - 1) * (1 + NF)) * kTile;
-                acc = fma(vs[0], __ldg(xs[s] + (size_t)p * ncp), acc);
+                const T *vs = v + (BANDW + NF + (s - 1) * (1 + NF)) * kTile;
+                acc = fma(vs[0], xc[s], acc);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) acc = fma(vs[(1 + f) * kTile], xf[s][f], acc);
             }
         }
-        const T *vu = v + (2 * WD + 1 + NF + (ns - 1) * (1 + NF)) * kTile;
-        for (int k = 0; k < nps; ++k) acc = fma(vu[k * kTile], __ldg(cc + (size_t)k * kTile), acc);
-        a.y[(size_t)p * ncp + cell] = acc;
-        __syncwarp();     // the stage is refilled by the next iteration's copy
+        const T *vu = v + (BANDW + NF + (ns - 1) * (1 + NF)) * kTile;
+        if (CREG) {
+            static_assert(kStructRegPairs == 8, "one case per slot");
+            const T *vo = vu - poff * kTile;
+            switch (poff) {
+                case 0: acc = fma(vo[0 * kTile], cq[0], acc); [[fallthrough]];
+                case 1: acc = fma(vo[1 * kTile], cq[1], acc); [[fallthrough]];
+                case 2: acc = fma(vo[2 * kTile], cq[2], acc); [[fallthrough]];
+                case 3: acc = fma(vo[3 * kTile], cq[3], acc); [[fallthrough]];
+                case 4: acc = fma(vo[4 * kTile], cq[4], acc); [[fallthrough]];
+                case 5: acc = fma(vo[5 * kTile], cq[5], acc); [[fallthrough]];
+                case 6: acc = fma(vo[6 * kTile], cq[6], acc); [[fallthrough]];
+                case 7: acc = fma(vo[7 * kTile], cq[7], acc); [[fallthrough]];
+                default: break;
+            }
+        } else {
+            for (int k = 0; k < nps; ++k) acc = fma(vu[k * kTile], __ldg(cc + (size_t)k * kTile), acc);
+        }
+        if (p > p0) {
+            *yp = ylag;
+            yp += ncp;
+        }
+        ylag = acc;
+        __syncwarp();     // every lane is done with the stage before it is refilled
+        if (p + 2 < p1) issue(p + 2);
     }
-    cp_async_wait<0>();
+    if (p1 > p0) *yp = ylag;
+    }
 }
 
 // Repack the public values into one stream of one direction.  Each stream
@@ -354,6 +428,7 @@ MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T
     a.x = x;
     a.y = y;
     a.c = c;
+    a.err = h->d_err;
     a.nbr = P.nbr;
     a.slot_mask = P.slot_mask;
     a.grp_rows = P.grp_rows;
@@ -397,17 +472,24 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
     const unsigned grid = (unsigned)((warps + 3) / 4);
     if (a.structured) {
         constexpr int kWarpsPerBlock = 2;      // two row stages per warp; small blocks pack the SM finely
-        const size_t smem = (size_t)kWarpsPerBlock * 2 * a.s_rl * kTile * sizeof(T);
+        const size_t smem = (size_t)kWarpsPerBlock * mv_struct_warp_bytes(a.s_rl, (int)sizeof(T));
         void (*kern)(MvArgs<T>) = nullptr;
+        const bool creg = a.n_pslots <= kStructRegPairs;
         switch (a.wd) {
-            case 0: kern = k_mv_struct<T, 0>; break;
-            case 1: kern = k_mv_struct<T, 1>; break;
-            case 2: kern = k_mv_struct<T, 2>; break;
-            case 3: kern = k_mv_struct<T, 3>; break;
-            default: kern = k_mv_struct<T, 4>; break;
+            case 0: kern = creg ? k_mv_struct<T, 0, true> : k_mv_struct<T, 0, false>; break;
+            case 1: kern = creg ? k_mv_struct<T, 1, true> : k_mv_struct<T, 1, false>; break;
+            case 2: kern = creg ? k_mv_struct<T, 2, true> : k_mv_struct<T, 2, false>; break;
+            case 3: kern = creg ? k_mv_struct<T, 3, true> : k_mv_struct<T, 3, false>; break;
+            default: kern = creg ? k_mv_struct<T, 4, true> : k_mv_struct<T, 4, false>; break;
         }
         if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * kTile, smem, h->stream>>>(a);
+        int per_sm = 0, dev = 0, nsm = 0;
+        STS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * kTile, smem));
+        STS_CK(cudaGetDevice(&dev));
+        STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const long long blocks = std::max(1LL, std::min(need, (long long)std::max(per_sm, 1) * nsm));
+        kern<<<(unsigned)blocks, kWarpsPerBlock * kTile, smem, h->stream>>>(a);
     } else {
         k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);
     }

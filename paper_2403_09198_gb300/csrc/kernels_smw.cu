@@ -296,145 +296,331 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
 //   tail:                 W[a][q] for the correction x = x0 - W C^-1 t.
 // The band recurrences keep their last W values in registers, so the only
 // dependency chain is one FMA per row.
+//
+// Stream layout.  Rows are packed in groups of whole 16-byte vectors (VEC =
+// 16 / sizeof(T) positions): a group is the least number of consecutive rows
+// of one section whose width is a multiple of VEC (rows past the end of the
+// section are zero), or one single row padded with zeros.  Groups never
+// straddle a chunk of K positions (8 KB), and each tile's stream is padded to
+// whole chunks, so one tile's stream is Lt contiguous positions stored as
+// [tile][position / VEC][lane][VEC]: a chunk is one bulk copy and a lane reads
+// VEC positions with one 16-byte shared-memory load.
 template <typename T>
 struct SApplyArgs {
-    const T *st;            // [len][ncp]
+    const T *st;            // [n_tiles][Lt / VEC][32][VEC]
     const double *Cinv;     // [r][r][ncp]
     const T *x;
     T *y;
-    int len, b, N, r, ncp, trans, n_tiles;
+    int *err;               // set when a bounded wait gave up
+    int Lt, b, N, r, ncp, trans, n_tiles;
 };
 
-constexpr int kApWarps = 4;     // warps per block of the structured apply (one per sub-partition)
-constexpr int kSApStages = 4;   // ring stages of the structured apply
+constexpr int kApWarps = 4;              // warps per block of the structured apply (one per sub-partition)
+constexpr int kSApStages = 5;            // ring stages of the structured apply (three chunks in flight)
+constexpr int kSApChunkBytes = 8192;     // bytes per stage (one bulk copy)
 
-// One block of kApWarps warps per SM; warp w of block k takes tiles
-// w * gridDim.x + k, + kApWarps * gridDim.x, ...  so that tiles are dealt to
-// SMs round-robin and no sub-partition runs two tiles while another idles.
+__host__ __device__ constexpr int sap_gcd(int a, int b) { return b == 0 ? a : sap_gcd(b, a % b); }
+// rows per group for rows of `width` positions, VEC positions per vector
+__host__ __device__ constexpr int sap_rows(int width, int vec) { return vec / sap_gcd(width, vec); }
+__host__ __device__ constexpr int sap_round(int n, int vec) { return (n + vec - 1) / vec * vec; }
+// tail rows per group: whole vectors and at least 8 positions
+__host__ __device__ constexpr int sap_tail_rows(int rmax, int vec) {
+    return sap_rows(rmax, vec) * rmax >= 8 ? sap_rows(rmax, vec) : 8 / rmax;
+}
+// shared memory of one warp: stages, 64 bytes of mbarriers, working vector [b][32]
+__host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
+    const size_t raw = (size_t)kSApStages * kSApChunkBytes + 64 + (size_t)b * kTile * elem;
+    return (raw + 127) / 128 * 128;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+__device__ __forceinline__ double vel(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vel(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+// One group of G positions in registers (G / VEC 16-byte loads).
+template <typename T, int G>
+struct Group {
+    using V = typename Vec16<T>::type;
+    static constexpr int VEC = 16 / (int)sizeof(T), NV = G / VEC;
+    static_assert(G % VEC == 0, "a group is whole vectors");
+    V v[NV];
+    __device__ __forceinline__ void load(const T *p) {
+        const V *q = reinterpret_cast<const V *>(p);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = q[j * kTile];
+    }
+    __device__ __forceinline__ T operator[](int k) const { return vel(v[k / VEC], k % VEC); }
+};
+
+// Warp w of block k takes tiles w * gridDim.x + k, + kApWarps * gridDim.x, ...
+// so that tiles are dealt to SMs round-robin and no sub-partition runs two
+// tiles while another idles.  The warp's tiles form one continuous stream for
+// its ring, so the next tile's first chunks arrive during the current tail;
+// the next tile's x is copied into the working vector row by row as the tail
+// frees it.  Within a section the next group (coefficients and working-vector
+// entries) is loaded into registers before the current one is used, so the
+// shared-memory latency overlaps the FMAs.
 template <typename T, int W, int RMAX>
 __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
-    constexpr int NF = kStructNF;
-    constexpr int FW = W + NF;                      // forward row width
-    constexpr int BW = 1 + NF + W + RMAX;           // backward row width
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5;
-    T *stg = reinterpret_cast<T *>(smem_raw) + (size_t)warp * (kSApStages * kApStage + a.b) * kTile;
-    T *ws = stg + kSApStages * kApStage * kTile;                // [b][32]: w, then x0
-    const int lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
-    for (int tile = warp * gridDim.x + blockIdx.x; tile < a.n_tiles; tile += nwarps * gridDim.x) {
-    const int cell = tile * kTile + lane;
+    constexpr int NF = kStructNF, VEC = 16 / (int)sizeof(T);
+    constexpr int K = kSApChunkBytes / (kTile * (int)sizeof(T));
+    constexpr int FW = W + NF, UF = sap_rows(FW, VEC), GF = UF * FW;
+    constexpr int GFF = sap_round(3, VEC), GBF = sap_round(6 + 3 * RMAX, VEC);
+    constexpr int BW = 1 + NF + W + RMAX, UB = sap_rows(BW, VEC), GB = UB * BW;
+    constexpr int UT = sap_tail_rows(RMAX, VEC), GT = UT * RMAX;
+    static_assert(GF <= K && GBF <= K && GB <= K && GT <= K, "groups fit a chunk");
+    static_assert(UF <= NF + 1, "forward rows read past N stay inside the block");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    unsigned char *mine = smem_raw + (size_t)warp * sap_warp_bytes(a.b, (int)sizeof(T));
+    T *stg = reinterpret_cast<T *>(mine);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mine + (size_t)kSApStages * kSApChunkBytes);
+    T *wl = reinterpret_cast<T *>(mine + (size_t)kSApStages * kSApChunkBytes + 64) + lane;  // row i at wl[i * 32]
+    const int gw = warp * gridDim.x + blockIdx.x, nw = nwarps * gridDim.x;
+    if (gw >= a.n_tiles) return;
+    const int my = (a.n_tiles - 1 - gw) / nw + 1;
     const size_t P = a.ncp;
-    const int N = a.N, r = a.r;
-    Ring<T, kApStage, kSApStages> R;
-    R.start(stg, a.st + (size_t)tile * kTile, P, a.len, lane);
-    const T *__restrict__ x = a.x;
-    for (int i = 0; i < a.b; ++i) ws[i * kTile + lane] = __ldg(x + i * P + cell);
-    // forward sweep: row i = [W band coefficients, oldest first | NF flow-row coefficients]
-    T win[W > 0 ? W : 1];
+    const int N = a.N, b = a.b, r = a.r;
+    BulkRing<T, K, kSApStages> R;
+    R.start(stg, bars, a.st, (size_t)a.Lt * kTile, gw, nw, my, a.Lt / K, lane);
+    for (int i = 0; i < b; ++i) cp_async_elem(wl + i * kTile, a.x + i * P + (size_t)gw * kTile + lane);
+    cp_async_commit();
+    for (int k = 0; k < my; ++k) {
+        const int cell = (gw + k * nw) * kTile + lane;
+        double cz[RMAX * RMAX];                 // C^-1 (transposed for A^T), zero outside r x r
 #pragma unroll
-    for (int k = 0; k < W; ++k) win[k] = T(0);
-    T accf[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) accf[f] = T(0);
-    for (int i = 0; i < N; ++i) {
-        const T *v = R.take(FW);
-        T acc = ws[i * kTile + lane];
-#pragma unroll
-        for (int k = 0; k < W; ++k) acc = fma(-v[k * kTile], win[k], acc);
-        ws[i * kTile + lane] = acc;
-#pragma unroll
-        for (int k = 0; k + 1 < W; ++k) win[k] = win[k + 1];
-        if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) accf[f] = fma(v[(W + f) * kTile], acc, accf[f]);
-    }
-    T wf[NF];
-    {
-        const T *v = R.take(3);                                 // (N+1,N), (N+2,N), (N+2,N+1)
-        wf[0] = ws[N * kTile + lane] - accf[0];
-        wf[1] = fma(-v[0], wf[0], ws[(N + 1) * kTile + lane] - accf[1]);
-        wf[2] = fma(-v[2 * kTile], wf[1], fma(-v[kTile], wf[0], ws[(N + 2) * kTile + lane] - accf[2]));
-    }
-    // backward sweep with t = V^T x0 accumulated on the way
-    T t[RMAX];
-#pragma unroll
-    for (int k = 0; k < RMAX; ++k) t[k] = T(0);
-    T xf[NF];
-    {
-        // [d2, V(N+2) | d1, u(N+1,N+2), V(N+1) | d0, u(N,N+1), u(N,N+2), V(N)], V padded to RMAX
-        const T *v = R.take(6 + 3 * RMAX);
-        xf[2] = v[0] * wf[2];
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) t[k] = fma(v[(1 + k) * kTile], xf[2], t[k]);
-        const T *v1 = v + (1 + RMAX) * kTile;
-        xf[1] = fma(-v1[kTile], xf[2], v1[0] * wf[1]);
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) t[k] = fma(v1[(2 + k) * kTile], xf[1], t[k]);
-        const T *v0 = v1 + (2 + RMAX) * kTile;
-        xf[0] = fma(-v0[2 * kTile], xf[2], fma(-v0[kTile], xf[1], v0[0] * wf[0]));
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) t[k] = fma(v0[(3 + k) * kTile], xf[0], t[k]);
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) ws[(N + f) * kTile + lane] = xf[f];
-    // backward row i = [pivot inverse | NF flow | W band, farthest first | V entries (RMAX)]
-    T xw[W > 0 ? W : 1];
-#pragma unroll
-    for (int k = 0; k < W; ++k) xw[k] = T(0);
-    for (int i = N - 1; i >= 0; --i) {
-        const T *v = R.take(BW);
-        T acc = v[0] * ws[i * kTile + lane];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) acc = fma(-v[(1 + f) * kTile], xf[f], acc);
-#pragma unroll
-        for (int k = 0; k < W; ++k) acc = fma(-v[(1 + NF + k) * kTile], xw[W - 1 - k], acc);
-        ws[i * kTile + lane] = acc;
-#pragma unroll
-        for (int k = W - 1; k > 0; --k) xw[k] = xw[k - 1];
-        if (W > 0) xw[0] = acc;
-#pragma unroll
-        for (int k = 0; k < RMAX; ++k) t[k] = fma(v[(1 + NF + W + k) * kTile], acc, t[k]);
-    }
-    // z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q])
-    T z[RMAX];
-#pragma unroll
-    for (int k = 0; k < RMAX; ++k) {
-        double sacc = 0.0;
-        if (k < r) {
+        for (int i = 0; i < RMAX; ++i)
 #pragma unroll
             for (int l = 0; l < RMAX; ++l)
-                if (l < r) {
-                    const double cij = a.trans ? __ldg(a.Cinv + ((size_t)l * r + k) * P + cell)
-                                               : __ldg(a.Cinv + ((size_t)k * r + l) * P + cell);
-                    sacc = fma(cij, (double)t[l], sacc);
-                }
-        }
-        z[k] = (T)sacc;
-    }
-    for (int q = 0; q < a.b; ++q) {
-        const T *v = R.take(RMAX);
-        T val = ws[q * kTile + lane];
+                cz[i * RMAX + l] = (i < r && l < r)
+                                       ? __ldg(a.Cinv + (a.trans ? (size_t)l * r + i : (size_t)i * r + l) * P + cell)
+                                       : 0.0;
+        cp_async_wait<0>();
+        __syncwarp();
+        // ---- forward sweep over the level rows
+        T win[W > 0 ? W : 1];
 #pragma unroll
-        for (int k = 0; k < RMAX; ++k) val = fma(-v[k * kTile], z[k], val);
-        a.y[q * P + cell] = val;
+        for (int q = 0; q < W; ++q) win[q] = T(0);
+        T accf[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) accf[f] = T(0);
+        {
+            const int ng = (N + UF - 1) / UF, nfull = N / UF;
+            Group<T, GF> gA, gB;
+            T xa[UF], xb[UF];
+            auto load = [&](Group<T, GF> &g, T (&xv)[UF], int grp) {
+                g.load(R.take(GF));
+#pragma unroll
+                for (int u = 0; u < UF; ++u) xv[u] = wl[(grp * UF + u) * kTile];
+            };
+            // w_i is stored one row late, when its FMA has long completed: a
+            // store waiting on a fresh FP64 result would hold up the warp
+            T lag = T(0);
+            int lag_i = -1;
+            auto row = [&](const Group<T, GF> &g, T acc, int u, int i) {
+#pragma unroll
+                for (int q = 0; q < W; ++q) acc = fma(-g[u * FW + q], win[q], acc);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) accf[f] = fma(g[u * FW + W + f], acc, accf[f]);
+                if (lag_i >= 0) wl[lag_i * kTile] = lag;
+                lag = acc;
+                lag_i = i;
+#pragma unroll
+                for (int q = 0; q + 1 < W; ++q) win[q] = win[q + 1];
+                if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
+            };
+            auto proc = [&](const Group<T, GF> &g, const T (&xv)[UF], int grp) {
+                if (grp < nfull) {
+#pragma unroll
+                    for (int u = 0; u < UF; ++u) row(g, xv[u], u, grp * UF + u);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < UF; ++u)
+                        if (grp * UF + u < N) row(g, xv[u], u, grp * UF + u);
+                }
+            };
+            load(gA, xa, 0);
+            for (int grp = 0; grp < ng; grp += 2) {
+                if (grp + 1 < ng) load(gB, xb, grp + 1);
+                proc(gA, xa, grp);
+                if (grp + 1 >= ng) break;
+                if (grp + 2 < ng) load(gA, xa, grp + 2);
+                proc(gB, xb, grp + 1);
+            }
+            if (lag_i >= 0) wl[lag_i * kTile] = lag;
+        }
+        // ---- forward flow rows: (N+1,N), (N+2,N), (N+2,N+1)
+        T wf[NF];
+        {
+            Group<T, GFF> g;
+            g.load(R.take(GFF));
+            wf[0] = wl[N * kTile] - accf[0];
+            wf[1] = fma(-g[0], wf[0], wl[(N + 1) * kTile] - accf[1]);
+            wf[2] = fma(-g[2], wf[1], fma(-g[1], wf[0], wl[(N + 2) * kTile] - accf[2]));
+        }
+        // ---- backward flow rows, with t = V^T x0 accumulated on the way
+        T t[RMAX];
+#pragma unroll
+        for (int q = 0; q < RMAX; ++q) t[q] = T(0);
+        T xf[NF];
+        {
+            // [d2, V(N+2) | d1, u(N+1,N+2), V(N+1) | d0, u(N,N+1), u(N,N+2), V(N)], V padded to RMAX
+            Group<T, GBF> g;
+            g.load(R.take(GBF));
+            xf[2] = g[0] * wf[2];
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[1 + q], xf[2], t[q]);
+            constexpr int o1 = 1 + RMAX, o0 = o1 + 2 + RMAX;
+            xf[1] = fma(-g[o1 + 1], xf[2], g[o1] * wf[1]);
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[o1 + 2 + q], xf[1], t[q]);
+            xf[0] = fma(-g[o0 + 2], xf[2], fma(-g[o0 + 1], xf[1], g[o0] * wf[0]));
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[o0 + 3 + q], xf[0], t[q]);
+        }
+        if (R.failed) goto fail;
+        // ---- backward level rows i = N-1 .. 0: [pivot inverse | NF flow | W band, farthest first | V (RMAX)]
+        {
+            T xw[W > 0 ? W : 1];
+#pragma unroll
+            for (int q = 0; q < W; ++q) xw[q] = T(0);
+            const int ng = (N + UB - 1) / UB, nfull = N / UB;
+            Group<T, GB> gA, gB;
+            T wa[UB], wb[UB];
+            auto load = [&](Group<T, GB> &g, T (&wv)[UB], int grp) {
+                g.load(R.take(GB));
+#pragma unroll
+                for (int u = 0; u < UB; ++u) wv[u] = wl[max(N - 1 - (grp * UB + u), 0) * kTile];
+            };
+            T lag = T(0);           // x0_i stored one row late (see the forward sweep)
+            int lag_i = -1;
+            auto row = [&](const Group<T, GB> &g, T wi, int u, int i) {
+                T acc = g[u * BW] * wi;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) acc = fma(-g[u * BW + 1 + f], xf[f], acc);
+#pragma unroll
+                for (int q = 0; q < W; ++q) acc = fma(-g[u * BW + 1 + NF + q], xw[W - 1 - q], acc);
+#pragma unroll
+                for (int q = 0; q < RMAX; ++q) t[q] = fma(g[u * BW + 1 + NF + W + q], acc, t[q]);
+                if (lag_i >= 0) wl[lag_i * kTile] = lag;
+                lag = acc;
+                lag_i = i;
+#pragma unroll
+                for (int q = W - 1; q > 0; --q) xw[q] = xw[q - 1];
+                if (W > 0) xw[0] = acc;
+            };
+            auto proc = [&](const Group<T, GB> &g, const T (&wv)[UB], int grp) {
+                if (grp < nfull) {
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) row(g, wv[u], u, N - 1 - (grp * UB + u));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < UB; ++u)
+                        if (grp * UB + u < N) row(g, wv[u], u, N - 1 - (grp * UB + u));
+                }
+            };
+            load(gA, wa, 0);
+            for (int grp = 0; grp < ng; grp += 2) {
+                if (grp + 1 < ng) load(gB, wb, grp + 1);
+                proc(gA, wa, grp);
+                if (grp + 1 >= ng) break;
+                if (grp + 2 < ng) load(gA, wa, grp + 2);
+                proc(gB, wb, grp + 1);
+            }
+            if (lag_i >= 0) wl[lag_i * kTile] = lag;
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) wl[(N + f) * kTile] = xf[f];
+        // ---- z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q])
+        {
+            T z[RMAX];
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                double s = 0.0;
+#pragma unroll
+                for (int l = 0; l < RMAX; ++l) s = fma(cz[i * RMAX + l], (double)t[l], s);
+                z[i] = (T)s;
+            }
+            const bool more = k + 1 < my;
+            const T *xn = a.x + (size_t)cell + (size_t)nw * kTile;
+            T *y = a.y + cell;
+            const int ng = (b + UT - 1) / UT;
+            Group<T, GT> gA, gB;
+            T va[UT], vb[UT];
+            const int nfull = b / UT;
+            auto load = [&](Group<T, GT> &g, T (&xv)[UT], int grp) {
+                g.load(R.take(GT));
+#pragma unroll
+                for (int u = 0; u < UT; ++u) xv[u] = wl[min(grp * UT + u, b - 1) * kTile];
+            };
+            T ylag = T(0);          // row q-1's result, stored during row q
+            int ylag_q = -1;
+            auto row = [&](const Group<T, GT> &g, T val, int u, int q) {
+#pragma unroll
+                for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
+                if (ylag_q >= 0) y[(size_t)ylag_q * P] = ylag;
+                ylag = val;
+                ylag_q = q;
+                if (more) cp_async_elem(wl + q * kTile, xn + (size_t)q * P);
+            };
+            auto proc = [&](const Group<T, GT> &g, const T (&xv)[UT], int grp) {
+                if (grp < nfull) {
+#pragma unroll
+                    for (int u = 0; u < UT; ++u) row(g, xv[u], u, grp * UT + u);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < UT; ++u)
+                        if (grp * UT + u < b) row(g, xv[u], u, grp * UT + u);
+                }
+            };
+            load(gA, va, 0);
+            for (int grp = 0; grp < ng; grp += 2) {
+                if (grp + 1 < ng) load(gB, vb, grp + 1);
+                proc(gA, va, grp);
+                if (grp + 1 >= ng) break;
+                if (grp + 2 < ng) load(gA, va, grp + 2);
+                proc(gB, vb, grp + 1);
+            }
+            if (ylag_q >= 0) y[(size_t)ylag_q * P] = ylag;
+            cp_async_commit();
+        }
+        if (R.failed) goto fail;
+        R.end_segment();
     }
-    R.finish();
-    __syncwarp();
-    }
+    return;
+fail:
+    if (lane == 0) atomicExch(a.err, 1);
+    R.drain();
+    cp_async_wait<0>();
 }
 
 // Structured stream packing: per position a source code and argument
 //   src >= 0: LU slot (times the pivot inverse of row arg if arg >= 0)
 //   src = -1: pivot inverse of row arg      src = -2: dot vector entry arg
 //   src = -3: W entry arg                   src = -4: zero
+// Output element i is (tile, vector, lane, element) of the layout above.
 template <typename T>
 __global__ void k_smw_spack(T *out, const double *lu, const double *dinv, const double *DV, const double *WW,
-                            const int *src, const int *arg, int len, int ncp) {
-    const long long total = (long long)len * ncp;
+                            const int *src, const int *arg, int Lt, int ncp) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const long long per_tile = (long long)Lt * kTile;
+    const long long total = per_tile * (ncp / kTile);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const int cell = (int)(i % ncp), pos = (int)(i / ncp);
+        const long long tile = i / per_tile;
+        const int e = (int)(i - tile * per_tile);
+        const int pv = e / (kTile * VEC), rem = e - pv * kTile * VEC;
+        const int lane = rem / VEC, pos = pv * VEC + rem % VEC;
+        const int cell = (int)tile * kTile + lane;
         const int sv = src[pos], ag = arg[pos];
         double v = 0.0;
         if (sv >= 0) {
@@ -613,7 +799,7 @@ sts_status smw_build(sts_jac_s *h) {
         if (desc.size() != pk_slot.size()) return set_error(STS_ERR_INVALID_ARG, "internal: apply program size");
         STS_TRY(upload(h, &M.ap_desc[dir], desc));
     }
-    // structured apply tables (both directions)
+    // structured apply tables (both directions; FP64 and, for mixed handles, FP32)
     const int sw = struct_band(b, h->dptr, h->didx);
     M.structured = sw >= 0 && h->r_diag <= 4 && M.nnz_lu == h->nnz_d;
     if (M.structured) {
@@ -621,76 +807,111 @@ sts_status smw_build(sts_jac_s *h) {
         M.s_w = sw;
         auto sl = [&](int i, int j) { return slot[(size_t)i * b + j]; };
         const int RMAX = r <= 2 ? 2 : 4;       // must match the kernel instance chosen at apply time
-        for (int dir = 0; dir < 2; ++dir) {
-            std::vector<int> src, arg, rsrc, rarg;
-            auto put = [&](int s_, int a_) { rsrc.push_back(s_); rarg.push_back(a_); };
-            // close one row: rows never straddle a kApStage chunk (zero padding)
-            auto row = [&]() {
-                const int width = (int)rsrc.size(), off = (int)(src.size() % kApStage);
-                if (off + width > kApStage)
-                    for (int k = off; k < kApStage; ++k) { src.push_back(-4); arg.push_back(0); }
-                src.insert(src.end(), rsrc.begin(), rsrc.end());
-                arg.insert(arg.end(), rarg.begin(), rarg.end());
-                rsrc.clear();
-                rarg.clear();
-            };
-            auto vd = [&](int q) {                  // dot-vector entries of unknown q, padded to RMAX
-                for (int k = 0; k < RMAX; ++k) put(k < r ? -2 : -4, k < r ? k * b + q : 0);
-            };
-            // lower factor of this direction: dir 0 L, dir 1 U'^T (U scaled by the row pivot inverse)
-            auto lo = [&](int i, int j) {           // coefficient (i, j), i > j
-                if (dir == 0) put(sl(i, j), -1);
-                else put(sl(j, i), j);
-            };
-            // upper factor after the pivot scaling: dir 0 U' = D^-1 U, dir 1 L^T
-            auto up = [&](int i, int j) {           // coefficient (i, j), i < j
-                if (dir == 0) put(sl(i, j), i);
-                else put(sl(j, i), -1);
-            };
-            for (int i = 0; i < N; ++i) {
-                for (int k = 0; k < sw; ++k) {
-                    const int j = i - sw + k;
-                    if (j >= 0) lo(i, j);
-                    else put(-4, 0);
+        for (int prec = 0; prec < 2; ++prec) {
+            if (prec == 1 && h->dtype != STS_MIXED) continue;
+            const int elem = prec == 0 ? 8 : 4, vec = 16 / elem, K = kSApChunkBytes / (kTile * elem);
+            for (int dir = 0; dir < 2; ++dir) {
+                std::vector<int> src, arg, gsrc, garg;
+                auto put = [&](int s_, int a_) { gsrc.push_back(s_); garg.push_back(a_); };
+                auto zero = [&](int n) { for (int k = 0; k < n; ++k) put(-4, 0); };
+                // close one group: whole vectors, never straddling a chunk (zero padding)
+                bool fits = true;
+                auto group = [&]() {
+                    while (gsrc.size() % vec) put(-4, 0);
+                    const int G = (int)gsrc.size(), off = (int)(src.size() % K);
+                    if (G > K) fits = false;
+                    if (off + G > K)
+                        for (int k = off; k < K; ++k) { src.push_back(-4); arg.push_back(0); }
+                    src.insert(src.end(), gsrc.begin(), gsrc.end());
+                    arg.insert(arg.end(), garg.begin(), garg.end());
+                    gsrc.clear();
+                    garg.clear();
+                };
+                auto vd = [&](int q) {              // dot-vector entries of unknown q, padded to RMAX
+                    for (int k = 0; k < RMAX; ++k) put(k < r ? -2 : -4, k < r ? k * b + q : 0);
+                };
+                // lower factor of this direction: dir 0 L, dir 1 U'^T (U scaled by the row pivot inverse)
+                auto lo = [&](int i, int j) {       // coefficient (i, j), i > j
+                    if (dir == 0) put(sl(i, j), -1);
+                    else put(sl(j, i), j);
+                };
+                // upper factor after the pivot scaling: dir 0 U' = D^-1 U, dir 1 L^T
+                auto up = [&](int i, int j) {       // coefficient (i, j), i < j
+                    if (dir == 0) put(sl(i, j), i);
+                    else put(sl(j, i), -1);
+                };
+                const int FW = sw + NF, UF = sap_rows(FW, vec);
+                for (int i0 = 0; i0 < N; i0 += UF) {
+                    for (int i = i0; i < i0 + UF; ++i) {
+                        if (i >= N) {
+                            zero(FW);
+                            continue;
+                        }
+                        for (int k = 0; k < sw; ++k) {
+                            const int j = i - sw + k;
+                            if (j >= 0) lo(i, j);
+                            else put(-4, 0);
+                        }
+                        for (int f = 0; f < NF; ++f) lo(N + f, i);
+                    }
+                    group();
                 }
-                for (int f = 0; f < NF; ++f) lo(N + f, i);
-                row();
-            }
-            lo(N + 1, N);
-            lo(N + 2, N);
-            lo(N + 2, N + 1);
-            row();
-            put(-1, N + 2);
-            vd(N + 2);
-            put(-1, N + 1);
-            up(N + 1, N + 2);
-            vd(N + 1);
-            put(-1, N);
-            up(N, N + 1);
-            up(N, N + 2);
-            vd(N);
-            row();
-            for (int i = N - 1; i >= 0; --i) {
-                put(-1, i);
-                for (int f = 0; f < NF; ++f) up(i, N + f);
-                for (int k = sw - 1; k >= 0; --k) {
-                    const int j = i + 1 + k;
-                    if (j < N) up(i, j);
-                    else put(-4, 0);
+                lo(N + 1, N);
+                lo(N + 2, N);
+                lo(N + 2, N + 1);
+                group();
+                put(-1, N + 2);
+                vd(N + 2);
+                put(-1, N + 1);
+                up(N + 1, N + 2);
+                vd(N + 1);
+                put(-1, N);
+                up(N, N + 1);
+                up(N, N + 2);
+                vd(N);
+                group();
+                const int BW = 1 + NF + sw + RMAX, UB = sap_rows(BW, vec);
+                for (int j0 = 0; j0 < N; j0 += UB) {
+                    for (int j = j0; j < j0 + UB; ++j) {
+                        const int i = N - 1 - j;
+                        if (i < 0) {
+                            zero(BW);
+                            continue;
+                        }
+                        put(-1, i);
+                        for (int f = 0; f < NF; ++f) up(i, N + f);
+                        for (int k = sw - 1; k >= 0; --k) {
+                            const int jj = i + 1 + k;
+                            if (jj < N) up(i, jj);
+                            else put(-4, 0);
+                        }
+                        vd(i);
+                    }
+                    group();
                 }
-                vd(i);
-                row();
+                const int UT = sap_tail_rows(RMAX, vec);
+                for (int q0 = 0; q0 < b; q0 += UT) {
+                    for (int q = q0; q < q0 + UT; ++q) {
+                        if (q >= b) {
+                            zero(RMAX);
+                            continue;
+                        }
+                        for (int k = 0; k < RMAX; ++k) put(k < r ? -3 : -4, k < r ? k * b + q : 0);
+                    }
+                    group();
+                }
+                while (src.size() % K) {
+                    src.push_back(-4);
+                    arg.push_back(0);
+                }
+                if (!fits) return set_error(STS_ERR_INVALID_ARG, "internal: structured apply group wider than a chunk");
+                for (size_t e = 0; e < src.size(); ++e)
+                    if (src[e] < -4 || (src[e] >= 0 && src[e] >= M.nnz_lu))
+                        return set_error(STS_ERR_INVALID_ARG, "internal: structured apply table");
+                M.s_lt[prec] = (int)src.size();
+                STS_TRY(upload(h, &M.spk_src[prec][dir], src));
+                STS_TRY(upload(h, &M.spk_arg[prec][dir], arg));
             }
-            for (int q = 0; q < b; ++q) {
-                for (int k = 0; k < RMAX; ++k) put(k < r ? -3 : -4, k < r ? k * b + q : 0);
-                row();
-            }
-            for (size_t e = 0; e < src.size(); ++e)
-                if (src[e] < -4 || (src[e] >= 0 && src[e] >= M.nnz_lu))
-                    return set_error(STS_ERR_INVALID_ARG, "internal: structured apply table");
-            M.s_len = (int)src.size();
-            STS_TRY(upload(h, &M.spk_src[dir], src));
-            STS_TRY(upload(h, &M.spk_arg[dir], arg));
         }
     }
     STS_TRY(upload(h, &M.lu_diag, M.h_lu_diag));
@@ -713,10 +934,11 @@ sts_status smw_build(sts_jac_s *h) {
     STS_TRY(dalloc(h, &M.Cinv, (size_t)std::max(r * r, 1) * P));
     for (int dir = 0; dir < 2; ++dir) {
         if (dir == 1 && !h->has_T) continue;
-        const size_t len = M.structured ? (size_t)M.s_len : (size_t)M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const size_t len = M.structured ? (size_t)M.s_lt[0] : (size_t)M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const size_t len32 = M.structured ? (size_t)M.s_lt[1] : len;
         STS_TRY(dalloc(h, &M.ap64[dir], len * P));
         if (h->dtype == STS_MIXED) {
-            STS_TRY(dalloc(h, &M.ap32[dir], len * P));
+            STS_TRY(dalloc(h, &M.ap32[dir], len32 * P));
             STS_TRY(dalloc(h, &M.W32[dir], (size_t)std::max(r, 1) * b * P));
             STS_TRY(dalloc(h, &M.DV32[dir], (size_t)std::max(r, 1) * b * P));
         }
@@ -774,21 +996,23 @@ sts_status smw_setup(sts_jac_s *h) {
         if (dir == 1 && !h->has_T) continue;
         const double *DV = dir == 0 ? M.Vd : M.Ud;
         const double *WW = dir == 0 ? M.W : M.Wt;
-        const int len = M.structured ? M.s_len : M.n_fwd[dir] + M.n_bwd[dir] + b;
-        const long long n = (long long)len * P;
         if (M.structured) {
-            k_smw_spack<double><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, DV, WW,
-                                                                          M.spk_src[dir], M.spk_arg[dir], len,
-                                                                          h->ncp);
+            const long long n64 = (long long)M.s_lt[0] * P;
+            k_smw_spack<double><<<grid_for(n64, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, DV, WW,
+                                                                            M.spk_src[0][dir], M.spk_arg[0][dir],
+                                                                            M.s_lt[0], h->ncp);
             STS_LAUNCHED();
             if (M.ap32[dir]) {
-                k_smw_spack<float><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap32[dir], M.lu, M.dinv, DV, WW,
-                                                                            M.spk_src[dir], M.spk_arg[dir], len,
-                                                                            h->ncp);
+                const long long n32 = (long long)M.s_lt[1] * P;
+                k_smw_spack<float><<<grid_for(n32, 256), 256, 0, h->stream>>>(M.ap32[dir], M.lu, M.dinv, DV, WW,
+                                                                              M.spk_src[1][dir], M.spk_arg[1][dir],
+                                                                              M.s_lt[1], h->ncp);
                 STS_LAUNCHED();
             }
             continue;
         }
+        const int len = M.n_fwd[dir] + M.n_bwd[dir] + b;
+        const long long n = (long long)len * P;
         k_smw_pack<double><<<grid_for(n, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, M.pk_slot[dir],
                                                                      M.pk_scale[dir], len, h->ncp);
         STS_LAUNCHED();
@@ -829,10 +1053,10 @@ template <typename T>
 static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T *z) {
     const SmwPlan &M = h->smw;
     SApplyArgs<T> a;
-    a.st = st; a.Cinv = M.Cinv; a.x = x; a.y = z;
-    a.len = M.s_len; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp; a.trans = dir;
-    a.n_tiles = h->n_tiles;
-    const size_t per_warp = ((size_t)kSApStages * kApStage + h->b) * kTile * sizeof(T);
+    a.st = st; a.Cinv = M.Cinv; a.x = x; a.y = z; a.err = h->d_err;
+    a.Lt = M.s_lt[sizeof(T) == 8 ? 0 : 1]; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp;
+    a.trans = dir; a.n_tiles = h->n_tiles;
+    const size_t per_warp = sap_warp_bytes(h->b, (int)sizeof(T));
     const int wpb = (int)std::min<size_t>(kApWarps, (size_t)(227 * 1024) / per_warp);
     if (wpb < 1)
         return set_error(STS_ERR_INVALID_ARG, "block size %d needs %zu bytes of shared memory per warp", h->b, per_warp);
@@ -850,7 +1074,7 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     int dev = 0, nsm = 0;
     STS_CK(cudaGetDevice(&dev));
     STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = std::max(1, std::min(nsm, h->n_tiles));
+    const int blocks = std::max(1, std::min(nsm, (h->n_tiles + wpb - 1) / wpb));
     kern<<<blocks, wpb * kTile, smem, h->stream>>>(a);
     STS_LAUNCHED();
     return STS_OK;

@@ -179,11 +179,12 @@ struct SmwPlan {
     int *err_cell = nullptr;     // device: first failing cell (INT_MAX if none)
     bool ready = false;
     // Structured apply (diagonal pattern of the paper's family, no fill): one
-    // coefficient stream per direction in ap64/ap32 of length s_len, packed
-    // from (spk_src, spk_arg) (see k_smw_spack).
+    // coefficient stream per direction and precision in ap64 / ap32, s_lt[prec]
+    // positions per tile, packed from (spk_src, spk_arg)[prec][dir] (see k_smw_spack).
     bool structured = false;
-    int s_w = 0, s_len = 0;
-    int *spk_src[2] = {nullptr, nullptr}, *spk_arg[2] = {nullptr, nullptr};
+    int s_w = 0, s_lt[2] = {0, 0};
+    int *spk_src[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int *spk_arg[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 // Dense-BSR baseline (Section 3.4 storage).
@@ -234,6 +235,7 @@ struct sts_jac_s {
     double *vin = nullptr, *vout = nullptr;     // [b*ncp] layout conversion buffers
     float *vin32 = nullptr, *vout32 = nullptr;
     double *c64 = nullptr;                      // matvec pair dots [n_tiles*n_pslots_max*32]
+    int *d_err = nullptr;                       // device: set when a bounded device wait gave up
     float *c32 = nullptr;
     double *g_c = nullptr;                      // adjoint: pair dots of the T direction
     int *g_pair_cN = nullptr, *g_pair_cT = nullptr, *g_pair_row = nullptr, *g_pair_col = nullptr;
@@ -275,6 +277,7 @@ sts_status from_internal32(sts_jac_s *h, const float *xi, float *x);
 sts_status smw_build(sts_jac_s *h);                       // host schedule + device tables
 sts_status smw_repack(sts_jac_s *h, const double *S, const double *U, const double *V);
 sts_status smw_setup(sts_jac_s *h);
+sts_status check_device(sts_jac_s *h);                   // STS_ERR_TIMEOUT if a bounded device wait gave up
 sts_status smw_apply64(sts_jac_s *h, int dir, const double *x, double *z);
 sts_status smw_apply32(sts_jac_s *h, int dir, const float *x, float *z);
 
