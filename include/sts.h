@@ -266,6 +266,16 @@ sts_status sts_jac_memory(sts_jac_t h, size_t *bytes);
  */
 sts_status sts_launch_count(unsigned long long *count);
 
+/*
+ * Self-test of the bounded device wait used by the bulk-copy rings (no paper
+ * counterpart): one warp waits on an mbarrier phase that nothing completes,
+ * gives up after about one second and reports it, as a real timed-out wait
+ * would.  Returns STS_ERR_TIMEOUT when the wait gave up and the device is
+ * still usable afterwards, STS_ERR_CUDA otherwise.  Synchronous on the given
+ * stream (NULL: the legacy default stream).
+ */
+sts_status sts_selftest_bounded_wait(void *stream);
+
 /* Destroy a handle and free its device memory.  NULL is accepted. */
 sts_status sts_jac_destroy(sts_jac_t h);
 

@@ -29,7 +29,8 @@ STS_PRECOND_BJ, STS_PRECOND_NONE = 0, 1
 ABI_FUNCTIONS = ["sts_last_error", "sts_version", "sts_jac_create", "sts_jac_update_values",
                  "sts_jac_matvec", "sts_jac_matvec_noalloc", "sts_jac_matvec_f32", "sts_jac_bjacobi_setup",
                  "sts_jac_bjacobi_apply", "sts_jac_bjacobi_apply_f32", "sts_gmres_solve",
-                 "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_jac_destroy"]
+                 "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_selftest_bounded_wait",
+                 "sts_jac_destroy"]
 
 
 class sts_jac_desc(ctypes.Structure):
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                 "sts_jac_grad": [P, P, P, P, P, P],
                 "sts_jac_memory": [P, ctypes.POINTER(ctypes.c_size_t)],
                 "sts_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
+                "sts_selftest_bounded_wait": [P],
                 "sts_jac_destroy": [P],
             }
             for name, args in sig.items():

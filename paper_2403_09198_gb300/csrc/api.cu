@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "ring.cuh"
 #include "sts_internal.h"
 
 namespace sts {
@@ -562,6 +563,18 @@ sts_status check_handle(sts_jac_t h, const void *a, const void *b, const char *f
     return STS_OK;
 }
 
+// One warp waits, through the rings' bounded wait, on a phase nothing completes.
+__global__ void k_wait_selftest(int *flag) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const bool done = mbar_wait_bounded(smem_addr(&bar), 0u);
+    if (threadIdx.x == 0) *flag = done ? 2 : 1;
+}
+
 }  // namespace
 
 // A bounded device wait (bulk copies into shared memory) gave up since the
@@ -684,6 +697,25 @@ sts_status sts_jac_grad(sts_jac_t h, const double *lambda, const double *x, doub
     if (h->rep != STS_REP_FACTORED || !h->has_T)
         return set_error(STS_ERR_INVALID_ARG, "sts_jac_grad: needs a factored handle with enable_transpose");
     STS_GUARD(return grad(h, lambda, x, gS, gU, gV);)
+}
+
+sts_status sts_selftest_bounded_wait(void *stream_) {
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    int *d_flag = nullptr, flag = 0;
+    if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess)
+        return set_error(STS_ERR_CUDA, "sts_selftest_bounded_wait: cudaMalloc failed");
+    cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), stream);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, kTile, 0, stream>>>(d_flag);
+        STS_LAUNCHED();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return set_error(STS_ERR_CUDA, "sts_selftest_bounded_wait: %s", cudaGetErrorString(e));
+    if (flag != 1) return set_error(STS_ERR_CUDA, "sts_selftest_bounded_wait: the wait did not give up (flag %d)", flag);
+    return set_error(STS_ERR_TIMEOUT, "sts_selftest_bounded_wait: the bounded wait gave up as expected");
 }
 
 sts_status sts_launch_count(unsigned long long *count) {
