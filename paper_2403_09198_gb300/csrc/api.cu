@@ -425,6 +425,7 @@ sts_status load_values(sts_jac_s *h, const double *S, const double *U, const dou
         st = mv_repack(h, 0, dS, dU, dV);
         if (st == STS_OK && h->has_T) st = mv_repack(h, 1, dS, dU, dV);
         if (st == STS_OK) st = smw_repack(h, dS, dU, dV);
+        h->streams_dirty = true;
     } else {
         st = dense_build(h, dS, dU, dV);
     }

@@ -29,6 +29,7 @@ struct MvArgs {
     T *y;                   // [b][ncp]
     T *c;                   // [n_tiles][n_dtasks][32]
     int *err;               // set when a bounded wait gave up
+    int pre;                // the coefficient streams may be read before the grid-dependency wait
     const int *nbr;         // [n_tiles][n_slots][32]
     const unsigned *slot_mask;
     const int *grp_rows;
@@ -61,20 +62,28 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
     if (wid >= (long long)a.n_tiles * a.n_dtasks) return;
     const int t = (int)(wid / a.n_dtasks), k = (int)(wid % a.n_dtasks);
     const int s = a.dtask_slot[k];
+    const bool present = (a.slot_mask[t] >> s) & 1u;
+    const int j = present ? a.nbr[((size_t)t * a.n_slots + s) * kTile + lane] : -1;
+    const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_dtasks + k) * a.Lp * kTile + lane;
+    T va[CH], xa[CH], vb[CH], xb[CH];
+    if (present && a.pre) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) va[i] = __ldg(dv + (size_t)i * kTile);
+    }
+    pdl_wait();
+    pdl_trigger();
     T acc = T(0);
-    if ((a.slot_mask[t] >> s) & 1u) {
-        const int j = a.nbr[((size_t)t * a.n_slots + s) * kTile + lane];
+    if (present) {
         // an absent neighbour reads the lane's own cell: its coefficients are zero
         const T *__restrict__ xj = a.x + (j >= 0 ? j : t * kTile + lane);
-        const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_dtasks + k) * a.Lp * kTile + lane;
         const int bm1 = a.b - 1;
         const size_t ncp = a.ncp;
-        T va[CH], xa[CH], vb[CH], xb[CH];
+        if (!a.pre) {
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            va[i] = __ldg(dv + (size_t)i * kTile);
-            xa[i] = __ldg(xj + (size_t)min(i, bm1) * ncp);
+            for (int i = 0; i < CH; ++i) va[i] = __ldg(dv + (size_t)i * kTile);
         }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) xa[i] = __ldg(xj + (size_t)min(i, bm1) * ncp);
         for (int base = 0; base < a.Lp; base += 2 * CH) {
             if (base + CH < a.Lp) {
 #pragma unroll
@@ -202,8 +211,26 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
     // persistent: warp items (tile, group) are dealt round-robin over the grid
     const long long n_items = (long long)a.n_tiles * a.n_groups;
     const long long wstep = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wid < n_items;
-         wid += wstep) {
+    const long long wid0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // the first item's first two rows are copied before the grid-dependency
+    // wait when the streams are not being written by the previous grid
+    bool primed = false;
+    if (a.pre && wid0 < n_items && (int)(wid0 % a.n_groups) != a.n_lgroups) {
+        const int t0 = (int)(wid0 / a.n_groups), q0 = (int)(wid0 % a.n_groups) * a.s_gl;
+        const int q1 = min(N, q0 + a.s_gl);
+        const T *src = a.main + ((size_t)t0 * a.tile_len + (size_t)q0 * RL) * kTile;
+        for (int r = q0; r < min(q0 + 2, q1); ++r)
+            if (lane == 0) {
+                const int sg = (r - q0) & 1;
+                mbar_expect_tx(bar + 8u * sg, row_bytes);
+                bulk_copy_g2s(smem_addr(stage0 + (size_t)sg * RL * kTile), src + (size_t)(r - q0) * RL * kTile,
+                              row_bytes, bar + 8u * sg);
+            }
+        primed = true;
+    }
+    pdl_wait();
+    pdl_trigger();
+    for (long long wid = wid0; wid < n_items; wid += wstep) {
     const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
     const size_t cell = (size_t)t * kTile + lane;
     const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
@@ -229,8 +256,11 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
                           row_bytes, bar + 8u * sg);
         }
     };
-    issue(p0);
-    if (p0 + 1 < p1) issue(p0 + 1);
+    if (!primed) {
+        issue(p0);
+        if (p0 + 1 < p1) issue(p0 + 1);
+    }
+    primed = false;
     const T *xs[NS];
     T xf[NS][NF];
 #pragma unroll
@@ -429,6 +459,7 @@ MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T
     a.y = y;
     a.c = c;
     a.err = h->d_err;
+    a.pre = h->streams_dirty ? 0 : 1;
     a.nbr = P.nbr;
     a.slot_mask = P.slot_mask;
     a.grp_rows = P.grp_rows;
@@ -462,6 +493,7 @@ sts_status dots_launch(sts_jac_s *h, const MvArgs<T> &a) {
     const long long warps = (long long)a.n_tiles * a.n_dtasks;
     k_dots<T><<<(unsigned)((warps + 3) / 4), 128, 0, h->stream>>>(a);
     STS_LAUNCHED();
+    h->streams_dirty = false;
     return STS_OK;
 }
 
@@ -489,6 +521,8 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
         STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
         const long long blocks = std::max(1LL, std::min(need, (long long)std::max(per_sm, 1) * nsm));
+        // an ordinary launch: with a programmatic early start the persistent
+        // blocks begin at different times during pass 1 and finish unevenly
         kern<<<(unsigned)blocks, kWarpsPerBlock * kTile, smem, h->stream>>>(a);
     } else {
         k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);

@@ -313,6 +313,7 @@ struct SApplyArgs {
     T *y;
     int *err;               // set when a bounded wait gave up
     int Lt, b, N, r, ncp, trans, n_tiles;
+    int pre;                // the stream and C^-1 may be read before the grid-dependency wait
 };
 
 constexpr int kApWarps = 4;              // warps per block of the structured apply (one per sub-partition)
@@ -391,7 +392,10 @@ __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
     const size_t P = a.ncp;
     const int N = a.N, b = a.b, r = a.r;
     BulkRing<T, K, kSApStages> R;
-    R.start(stg, bars, a.st, (size_t)a.Lt * kTile, gw, nw, my, a.Lt / K, lane);
+    R.start(stg, bars, a.st, (size_t)a.Lt * kTile, gw, nw, my, a.Lt / K, lane, a.pre != 0);
+    pdl_wait();
+    pdl_trigger();
+    if (!a.pre) R.prime();
     for (int i = 0; i < b; ++i) cp_async_elem(wl + i * kTile, a.x + i * P + (size_t)gw * kTile + lane);
     cp_async_commit();
     for (int k = 0; k < my; ++k) {
@@ -1030,6 +1034,7 @@ sts_status smw_setup(sts_jac_s *h) {
         }
     }
     M.ready = true;
+    h->streams_dirty = true;
     return STS_OK;
 }
 
@@ -1056,6 +1061,7 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     a.st = st; a.Cinv = M.Cinv; a.x = x; a.y = z; a.err = h->d_err;
     a.Lt = M.s_lt[sizeof(T) == 8 ? 0 : 1]; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp;
     a.trans = dir; a.n_tiles = h->n_tiles;
+    a.pre = h->streams_dirty ? 0 : 1;
     const size_t per_warp = sap_warp_bytes(h->b, (int)sizeof(T));
     const int wpb = (int)std::min<size_t>(kApWarps, (size_t)(227 * 1024) / per_warp);
     if (wpb < 1)
@@ -1075,8 +1081,9 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     STS_CK(cudaGetDevice(&dev));
     STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(nsm, (h->n_tiles + wpb - 1) / wpb));
-    kern<<<blocks, wpb * kTile, smem, h->stream>>>(a);
+    STS_CK(launch_pdl(kern, dim3(blocks), dim3(wpb * kTile), smem, h->stream, a));
     STS_LAUNCHED();
+    h->streams_dirty = false;
     return STS_OK;
 }
 

@@ -104,6 +104,15 @@ struct Ring {
     __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
 };
 
+// Programmatic dependent launch.  pdl_wait returns once the grids this one
+// depends on have completed and their writes are visible (immediately when
+// the launch had no such dependency); pdl_trigger lets the next grid on the
+// stream start.  Kernels of this library trigger only after their own wait,
+// so a kernel that starts early knows every grid before its predecessor has
+// completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Bulk copies completed on mbarriers.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -186,9 +195,10 @@ struct BulkRing {
         }
         ++issued;
     }
-    // Barriers are initialised by lane 0; the first S-2 chunks are issued.
+    // Barriers are initialised by lane 0; the first S-2 chunks are issued
+    // (now, or by prime() when the source may not be read yet).
     __device__ __forceinline__ void start(T *stg_, uint64_t *bars, const T *src_, size_t seg_elems_, int seg0_,
-                                          int seg_step_, int nseg, int nch_, int lane_) {
+                                          int seg_step_, int nseg, int nch_, int lane_, bool issue_now = true) {
         stg = stg_;
         bar = smem_addr(bars);
         src = src_;
@@ -212,6 +222,9 @@ struct BulkRing {
             mbar_init_fence();
         }
         __syncwarp();
+        if (issue_now) prime();
+    }
+    __device__ __forceinline__ void prime() {
         for (int c = 0; c < S - 2 && issued < total; ++c) issue();
     }
     // Make chunk c current (waiting for it) and refill the stage of c - 2.

@@ -68,6 +68,26 @@ sts_status set_error(sts_status s, const char *fmt, ...);
 extern std::atomic<unsigned long long> g_launches;
 
 // After every kernel launch: count it and surface launch errors.
+// Launch with programmatic dependent launch allowed: the kernel may start
+// while the previous kernel on the stream finishes, and must call
+// griddepcontrol.wait (pdl_wait) before it reads anything an earlier kernel
+// may still write or writes anything an earlier kernel may still read.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #define STS_LAUNCHED()                                                    \
     do {                                                                  \
         ::sts::g_launches.fetch_add(1, std::memory_order_relaxed);        \
@@ -221,6 +241,10 @@ struct sts_jac_s {
     bool has_T = false;
     long long nnz_S = 0;
     cudaStream_t stream = nullptr;
+    // The last launch of this handle wrote its coefficient streams (values
+    // update or block-Jacobi setup): the next hot kernel must not read them
+    // before its grid-dependency wait.
+    bool streams_dirty = true;
     // host copies of the structure
     std::vector<int> bptr, bidx, dptr, didx, optr, oidx;
     std::vector<long long> soff;    // [nnzb+1]
