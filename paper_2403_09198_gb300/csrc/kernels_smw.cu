@@ -324,13 +324,24 @@ __host__ __device__ constexpr int sap_gcd(int a, int b) { return b == 0 ? a : sa
 // rows per group for rows of `width` positions, VEC positions per vector
 __host__ __device__ constexpr int sap_rows(int width, int vec) { return vec / sap_gcd(width, vec); }
 __host__ __device__ constexpr int sap_round(int n, int vec) { return (n + vec - 1) / vec * vec; }
-// tail rows per group: whole vectors and at least 8 positions
-__host__ __device__ constexpr int sap_tail_rows(int rmax, int vec) {
-    return sap_rows(rmax, vec) * rmax >= 8 ? sap_rows(rmax, vec) : 8 / rmax;
+// Rows per group: the fewest rows of whole vectors, repeated up to at least 16
+// positions (the per-group bookkeeping is then spread over 16 or more FMAs);
+// forward groups hold at most NF + 1 rows, so that their working-vector reads
+// past the last level row stay inside the block.
+__host__ __device__ constexpr int sap_group_rows(int width, int vec) {
+    return sap_rows(width, vec) * ((16 + sap_rows(width, vec) * width - 1) / (sap_rows(width, vec) * width));
 }
-// shared memory of one warp: stages, 64 bytes of mbarriers, working vector [b][32]
+__host__ __device__ constexpr int sap_fwd_rows(int width, int vec, int nf) {
+    return sap_group_rows(width, vec) <= nf + 1 ? sap_group_rows(width, vec)
+                                                : (sap_rows(width, vec) > nf + 1 ? sap_rows(width, vec) : nf + 1 -
+                                                   (nf + 1) % sap_rows(width, vec));
+}
+// shared memory of one consumer warp: stages, 128 bytes of mbarriers (full,
+// empty), working vector [b][32]
+constexpr int kSApBarBytes = 128;
+static_assert(2 * 8 * kSApStages <= kSApBarBytes, "full and empty barriers fit");
 __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
-    const size_t raw = (size_t)kSApStages * kSApChunkBytes + 64 + (size_t)b * kTile * elem;
+    const size_t raw = (size_t)kSApStages * kSApChunkBytes + kSApBarBytes + (size_t)b * kTile * elem;
     return (raw + 127) / 128 * 128;
 }
 
@@ -362,40 +373,142 @@ struct Group {
     __device__ __forceinline__ T operator[](int k) const { return vel(v[k / VEC], k % VEC); }
 };
 
-// Warp w of block k takes tiles w * gridDim.x + k, + kApWarps * gridDim.x, ...
-// so that tiles are dealt to SMs round-robin and no sub-partition runs two
-// tiles while another idles.  The warp's tiles form one continuous stream for
-// its ring, so the next tile's first chunks arrive during the current tail;
-// the next tile's x is copied into the working vector row by row as the tail
-// frees it.  Within a section the next group (coefficients and working-vector
-// entries) is loaded into registers before the current one is used, so the
-// shared-memory latency overlaps the FMAs.
+// One section of rows (forward level rows, backward level rows or tail) in
+// groups of U rows of G stream positions.  The next group's coefficients and
+// working-vector entries are loaded into registers before the current group
+// is processed.  wsrow(j): working-vector row read for section row j;
+// row(g, w, u, j): computes section row j (row u of group g, working-vector
+// entry w) and returns its result; put(j, v) stores the result of section row
+// j, one row late, when its FP64 FMA has long completed.
+template <typename T, int G, int U, typename RingT, typename WsRow, typename RowF, typename PutF>
+__device__ __forceinline__ void sap_section(RingT &R, const T *wl, int nrows, WsRow wsrow, RowF row, PutF put) {
+    const int ng = (nrows + U - 1) / U, nfull = nrows / U;
+    Group<T, G> gA, gB;
+    T xa[U], xb[U];
+    T carry = T(0);
+    auto load = [&](Group<T, G> &g, T (&xv)[U], int grp) {
+        g.load(R.take(G));
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = wl[wsrow(grp * U + u) * kTile];
+    };
+    auto proc = [&](const Group<T, G> &g, const T (&xv)[U], int grp) {
+        T prev = carry;
+        if (grp < nfull) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const T v = row(g, xv[u], u, grp * U + u);
+                if (u > 0 || grp > 0) put(grp * U + u - 1, prev);
+                prev = v;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (grp * U + u < nrows) {
+                    const T v = row(g, xv[u], u, grp * U + u);
+                    if (u > 0 || grp > 0) put(grp * U + u - 1, prev);
+                    prev = v;
+                }
+        }
+        carry = prev;
+    };
+    if (nrows <= 0) return;
+    load(gA, xa, 0);
+    for (int grp = 0; grp < ng; grp += 2) {
+        if (grp + 1 < ng) load(gB, xb, grp + 1);
+        proc(gA, xa, grp);
+        if (grp + 1 >= ng) break;
+        if (grp + 2 < ng) load(gA, xa, grp + 2);
+        proc(gB, xb, grp + 1);
+    }
+    put(nrows - 1, carry);
+}
+
+// Consumer warp w of block k takes tiles w * gridDim.x + k, + nc * gridDim.x,
+// ... so that tiles are dealt to SMs round-robin and no sub-partition runs two
+// tiles while another idles; the block's last warp is the producer, whose
+// lane 0 issues every bulk copy of the block's rings.  A consumer's tiles form
+// one continuous stream for its ring, so the next tile's first chunks arrive
+// during the current tail; the next tile's x is copied into the working vector
+// row by row as the tail frees it.  Within a section the next group
+// (coefficients and working-vector entries) is loaded into registers before
+// the current one is used, so the shared-memory latency overlaps the FMAs.
 template <typename T, int W, int RMAX>
-__global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
+__global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T> a) {
     constexpr int NF = kStructNF, VEC = 16 / (int)sizeof(T);
     constexpr int K = kSApChunkBytes / (kTile * (int)sizeof(T));
-    constexpr int FW = W + NF, UF = sap_rows(FW, VEC), GF = UF * FW;
+    constexpr int FW = W + NF, UF = sap_fwd_rows(FW, VEC, NF), GF = UF * FW;
     constexpr int GFF = sap_round(3, VEC), GBF = sap_round(6 + 3 * RMAX, VEC);
-    constexpr int BW = 1 + NF + W + RMAX, UB = sap_rows(BW, VEC), GB = UB * BW;
-    constexpr int UT = sap_tail_rows(RMAX, VEC), GT = UT * RMAX;
+    constexpr int BW = 1 + NF + W + RMAX, UB = sap_group_rows(BW, VEC), GB = UB * BW;
+    constexpr int UT = sap_group_rows(RMAX, VEC), GT = UT * RMAX;
+    static_assert(GF % VEC == 0 && GB % VEC == 0 && GT % VEC == 0, "groups are whole vectors");
     static_assert(GF <= K && GBF <= K && GB <= K && GT <= K, "groups fit a chunk");
     static_assert(UF <= NF + 1, "forward rows read past N stay inside the block");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    unsigned char *mine = smem_raw + (size_t)warp * sap_warp_bytes(a.b, (int)sizeof(T));
-    T *stg = reinterpret_cast<T *>(mine);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(mine + (size_t)kSApStages * kSApChunkBytes);
-    T *wl = reinterpret_cast<T *>(mine + (size_t)kSApStages * kSApChunkBytes + 64) + lane;  // row i at wl[i * 32]
-    const int gw = warp * gridDim.x + blockIdx.x, nw = nwarps * gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nc = (int)(blockDim.x >> 5) - 1;                  // consumer warps
+    const size_t wbytes = sap_warp_bytes(a.b, (int)sizeof(T));
+    const int nw = nc * gridDim.x;
+    const int nch = a.Lt / K;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < nc; ++w) {
+            const uint32_t full = smem_addr(smem_raw + (size_t)w * wbytes + (size_t)kSApStages * kSApChunkBytes);
+#pragma unroll
+            for (int st = 0; st < kSApStages; ++st) {
+                mbar_init(full + 8u * st, 1);
+                mbar_init(full + 8u * (kSApStages + st), 32);
+            }
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (warp == nc) {
+        // ---- producer
+        if (lane == 0) {
+            RingProducer<T, K, kSApStages, kApWarps> pr;
+            pr.src = a.st;
+            pr.seg_elems = (size_t)a.Lt * kTile;
+            pr.nc = nc;
+            pr.seg_step = nw;
+            pr.nch = nch;
+            pr.maxc = 0;
+#pragma unroll
+            for (int w = 0; w < kApWarps; ++w) {
+                unsigned char *reg = smem_raw + (size_t)min(w, nc - 1) * wbytes;
+                pr.stg[w] = reinterpret_cast<T *>(reg);
+                pr.full[w] = smem_addr(reg + (size_t)kSApStages * kSApChunkBytes);
+                pr.empty[w] = pr.full[w] + 8u * kSApStages;
+                pr.seg0[w] = w * gridDim.x + blockIdx.x;
+                pr.nseg[w] = (w < nc && pr.seg0[w] < a.n_tiles) ? (a.n_tiles - 1 - pr.seg0[w]) / nw + 1 : 0;
+                pr.issued[w] = 0;
+                pr.pk[w] = 0;
+                pr.pl[w] = 0;
+                pr.maxc = max(pr.maxc, pr.nseg[w] * nch);
+            }
+            bool ok = a.pre ? pr.issue_upto(kSApStages) : true;
+            pdl_wait();
+            pdl_trigger();
+            if (ok) ok = pr.run();
+            if (!ok) atomicExch(a.err, 1);
+            pr.drain();
+        } else {
+            pdl_wait();
+            pdl_trigger();
+        }
+        return;
+    }
+    // ---- consumers
+    const int gw = warp * gridDim.x + blockIdx.x;
     if (gw >= a.n_tiles) return;
     const int my = (a.n_tiles - 1 - gw) / nw + 1;
     const size_t P = a.ncp;
     const int N = a.N, b = a.b, r = a.r;
-    BulkRing<T, K, kSApStages> R;
-    R.start(stg, bars, a.st, (size_t)a.Lt * kTile, gw, nw, my, a.Lt / K, lane, a.pre != 0);
+    unsigned char *mine = smem_raw + (size_t)warp * wbytes;
+    const uint32_t full = smem_addr(mine + (size_t)kSApStages * kSApChunkBytes);
+    T *wl = reinterpret_cast<T *>(mine + (size_t)kSApStages * kSApChunkBytes + kSApBarBytes) + lane;  // row i at wl[i * 32]
+    RingConsumer<T, K, kSApStages> R;
+    R.start(reinterpret_cast<T *>(mine), full, full + 8u * kSApStages, lane);
     pdl_wait();
     pdl_trigger();
-    if (!a.pre) R.prime();
     for (int i = 0; i < b; ++i) cp_async_elem(wl + i * kTile, a.x + i * P + (size_t)gw * kTile + lane);
     cp_async_commit();
     for (int k = 0; k < my; ++k) {
@@ -410,58 +523,26 @@ __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
                                        : 0.0;
         cp_async_wait<0>();
         __syncwarp();
-        // ---- forward sweep over the level rows
+        // ---- forward sweep over the level rows: row i = [W band, oldest first | NF flow]
         T win[W > 0 ? W : 1];
 #pragma unroll
         for (int q = 0; q < W; ++q) win[q] = T(0);
         T accf[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) accf[f] = T(0);
-        {
-            const int ng = (N + UF - 1) / UF, nfull = N / UF;
-            Group<T, GF> gA, gB;
-            T xa[UF], xb[UF];
-            auto load = [&](Group<T, GF> &g, T (&xv)[UF], int grp) {
-                g.load(R.take(GF));
-#pragma unroll
-                for (int u = 0; u < UF; ++u) xv[u] = wl[(grp * UF + u) * kTile];
-            };
-            // w_i is stored one row late, when its FMA has long completed: a
-            // store waiting on a fresh FP64 result would hold up the warp
-            T lag = T(0);
-            int lag_i = -1;
-            auto row = [&](const Group<T, GF> &g, T acc, int u, int i) {
+        sap_section<T, GF, UF>(
+            R, wl, N, [&](int j) { return min(j, b - 1); },
+            [&](const Group<T, GF> &g, T acc, int u, int) {
 #pragma unroll
                 for (int q = 0; q < W; ++q) acc = fma(-g[u * FW + q], win[q], acc);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) accf[f] = fma(g[u * FW + W + f], acc, accf[f]);
-                if (lag_i >= 0) wl[lag_i * kTile] = lag;
-                lag = acc;
-                lag_i = i;
 #pragma unroll
                 for (int q = 0; q + 1 < W; ++q) win[q] = win[q + 1];
                 if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
-            };
-            auto proc = [&](const Group<T, GF> &g, const T (&xv)[UF], int grp) {
-                if (grp < nfull) {
-#pragma unroll
-                    for (int u = 0; u < UF; ++u) row(g, xv[u], u, grp * UF + u);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < UF; ++u)
-                        if (grp * UF + u < N) row(g, xv[u], u, grp * UF + u);
-                }
-            };
-            load(gA, xa, 0);
-            for (int grp = 0; grp < ng; grp += 2) {
-                if (grp + 1 < ng) load(gB, xb, grp + 1);
-                proc(gA, xa, grp);
-                if (grp + 1 >= ng) break;
-                if (grp + 2 < ng) load(gA, xa, grp + 2);
-                proc(gB, xb, grp + 1);
-            }
-            if (lag_i >= 0) wl[lag_i * kTile] = lag;
-        }
+                return acc;
+            },
+            [&](int j, T v) { wl[j * kTile] = v; });
         // ---- forward flow rows: (N+1,N), (N+2,N), (N+2,N+1)
         T wf[NF];
         {
@@ -492,55 +573,27 @@ __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
             for (int q = 0; q < RMAX; ++q) t[q] = fma(g[o0 + 3 + q], xf[0], t[q]);
         }
         if (R.failed) goto fail;
-        // ---- backward level rows i = N-1 .. 0: [pivot inverse | NF flow | W band, farthest first | V (RMAX)]
+        // ---- backward level rows i = N-1-j: [pivot inverse | NF flow | W band, farthest first | V (RMAX)]
         {
             T xw[W > 0 ? W : 1];
 #pragma unroll
             for (int q = 0; q < W; ++q) xw[q] = T(0);
-            const int ng = (N + UB - 1) / UB, nfull = N / UB;
-            Group<T, GB> gA, gB;
-            T wa[UB], wb[UB];
-            auto load = [&](Group<T, GB> &g, T (&wv)[UB], int grp) {
-                g.load(R.take(GB));
+            sap_section<T, GB, UB>(
+                R, wl, N, [&](int j) { return max(N - 1 - j, 0); },
+                [&](const Group<T, GB> &g, T wi, int u, int) {
+                    T acc = g[u * BW] * wi;
 #pragma unroll
-                for (int u = 0; u < UB; ++u) wv[u] = wl[max(N - 1 - (grp * UB + u), 0) * kTile];
-            };
-            T lag = T(0);           // x0_i stored one row late (see the forward sweep)
-            int lag_i = -1;
-            auto row = [&](const Group<T, GB> &g, T wi, int u, int i) {
-                T acc = g[u * BW] * wi;
+                    for (int f = 0; f < NF; ++f) acc = fma(-g[u * BW + 1 + f], xf[f], acc);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) acc = fma(-g[u * BW + 1 + f], xf[f], acc);
+                    for (int q = 0; q < W; ++q) acc = fma(-g[u * BW + 1 + NF + q], xw[W - 1 - q], acc);
 #pragma unroll
-                for (int q = 0; q < W; ++q) acc = fma(-g[u * BW + 1 + NF + q], xw[W - 1 - q], acc);
+                    for (int q = 0; q < RMAX; ++q) t[q] = fma(g[u * BW + 1 + NF + W + q], acc, t[q]);
 #pragma unroll
-                for (int q = 0; q < RMAX; ++q) t[q] = fma(g[u * BW + 1 + NF + W + q], acc, t[q]);
-                if (lag_i >= 0) wl[lag_i * kTile] = lag;
-                lag = acc;
-                lag_i = i;
-#pragma unroll
-                for (int q = W - 1; q > 0; --q) xw[q] = xw[q - 1];
-                if (W > 0) xw[0] = acc;
-            };
-            auto proc = [&](const Group<T, GB> &g, const T (&wv)[UB], int grp) {
-                if (grp < nfull) {
-#pragma unroll
-                    for (int u = 0; u < UB; ++u) row(g, wv[u], u, N - 1 - (grp * UB + u));
-                } else {
-#pragma unroll
-                    for (int u = 0; u < UB; ++u)
-                        if (grp * UB + u < N) row(g, wv[u], u, N - 1 - (grp * UB + u));
-                }
-            };
-            load(gA, wa, 0);
-            for (int grp = 0; grp < ng; grp += 2) {
-                if (grp + 1 < ng) load(gB, wb, grp + 1);
-                proc(gA, wa, grp);
-                if (grp + 1 >= ng) break;
-                if (grp + 2 < ng) load(gA, wa, grp + 2);
-                proc(gB, wb, grp + 1);
-            }
-            if (lag_i >= 0) wl[lag_i * kTile] = lag;
+                    for (int q = W - 1; q > 0; --q) xw[q] = xw[q - 1];
+                    if (W > 0) xw[0] = acc;
+                    return acc;
+                },
+                [&](int j, T v) { wl[(N - 1 - j) * kTile] = v; });
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) wl[(N + f) * kTile] = xf[f];
@@ -549,52 +602,25 @@ __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
             T z[RMAX];
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
-                double s = 0.0;
+                double sacc = 0.0;
 #pragma unroll
-                for (int l = 0; l < RMAX; ++l) s = fma(cz[i * RMAX + l], (double)t[l], s);
-                z[i] = (T)s;
+                for (int l = 0; l < RMAX; ++l) sacc = fma(cz[i * RMAX + l], (double)t[l], sacc);
+                z[i] = (T)sacc;
             }
             const bool more = k + 1 < my;
             const T *xn = a.x + (size_t)cell + (size_t)nw * kTile;
             T *y = a.y + cell;
-            const int ng = (b + UT - 1) / UT;
-            Group<T, GT> gA, gB;
-            T va[UT], vb[UT];
-            const int nfull = b / UT;
-            auto load = [&](Group<T, GT> &g, T (&xv)[UT], int grp) {
-                g.load(R.take(GT));
+            sap_section<T, GT, UT>(
+                R, wl, b, [&](int j) { return min(j, b - 1); },
+                [&](const Group<T, GT> &g, T val, int u, int) {
 #pragma unroll
-                for (int u = 0; u < UT; ++u) xv[u] = wl[min(grp * UT + u, b - 1) * kTile];
-            };
-            T ylag = T(0);          // row q-1's result, stored during row q
-            int ylag_q = -1;
-            auto row = [&](const Group<T, GT> &g, T val, int u, int q) {
-#pragma unroll
-                for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
-                if (ylag_q >= 0) y[(size_t)ylag_q * P] = ylag;
-                ylag = val;
-                ylag_q = q;
-                if (more) cp_async_elem(wl + q * kTile, xn + (size_t)q * P);
-            };
-            auto proc = [&](const Group<T, GT> &g, const T (&xv)[UT], int grp) {
-                if (grp < nfull) {
-#pragma unroll
-                    for (int u = 0; u < UT; ++u) row(g, xv[u], u, grp * UT + u);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < UT; ++u)
-                        if (grp * UT + u < b) row(g, xv[u], u, grp * UT + u);
-                }
-            };
-            load(gA, va, 0);
-            for (int grp = 0; grp < ng; grp += 2) {
-                if (grp + 1 < ng) load(gB, vb, grp + 1);
-                proc(gA, va, grp);
-                if (grp + 1 >= ng) break;
-                if (grp + 2 < ng) load(gA, va, grp + 2);
-                proc(gB, vb, grp + 1);
-            }
-            if (ylag_q >= 0) y[(size_t)ylag_q * P] = ylag;
+                    for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
+                    return val;
+                },
+                [&](int j, T v) {
+                    y[(size_t)j * P] = v;
+                    if (more) cp_async_elem(wl + j * kTile, xn + (size_t)j * P);
+                });
             cp_async_commit();
         }
         if (R.failed) goto fail;
@@ -602,8 +628,8 @@ __global__ void __launch_bounds__(kApWarps * 32) k_smw_sapply(SApplyArgs<T> a) {
     }
     return;
 fail:
+    // the producer waits (bounded) for every copy it issued before it exits
     if (lane == 0) atomicExch(a.err, 1);
-    R.drain();
     cp_async_wait<0>();
 }
 
@@ -844,7 +870,7 @@ sts_status smw_build(sts_jac_s *h) {
                     if (dir == 0) put(sl(i, j), i);
                     else put(sl(j, i), -1);
                 };
-                const int FW = sw + NF, UF = sap_rows(FW, vec);
+                const int FW = sw + NF, UF = sap_fwd_rows(FW, vec, NF);
                 for (int i0 = 0; i0 < N; i0 += UF) {
                     for (int i = i0; i < i0 + UF; ++i) {
                         if (i >= N) {
@@ -874,7 +900,7 @@ sts_status smw_build(sts_jac_s *h) {
                 up(N, N + 2);
                 vd(N);
                 group();
-                const int BW = 1 + NF + sw + RMAX, UB = sap_rows(BW, vec);
+                const int BW = 1 + NF + sw + RMAX, UB = sap_group_rows(BW, vec);
                 for (int j0 = 0; j0 < N; j0 += UB) {
                     for (int j = j0; j < j0 + UB; ++j) {
                         const int i = N - 1 - j;
@@ -893,7 +919,7 @@ sts_status smw_build(sts_jac_s *h) {
                     }
                     group();
                 }
-                const int UT = sap_tail_rows(RMAX, vec);
+                const int UT = sap_group_rows(RMAX, vec);
                 for (int q0 = 0; q0 < b; q0 += UT) {
                     for (int q = q0; q < q0 + UT; ++q) {
                         if (q >= b) {
@@ -1081,7 +1107,7 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     STS_CK(cudaGetDevice(&dev));
     STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(nsm, (h->n_tiles + wpb - 1) / wpb));
-    STS_CK(launch_pdl(kern, dim3(blocks), dim3(wpb * kTile), smem, h->stream, a));
+    STS_CK(launch_pdl(kern, dim3(blocks), dim3((wpb + 1) * kTile), smem, h->stream, a));
     STS_LAUNCHED();
     h->streams_dirty = false;
     return STS_OK;

@@ -154,90 +154,54 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return true;
 }
 
-// Per-warp ring over a sequence of equal-length segments (one per tile the
-// warp processes): segment k starts at src + (seg0 + k * seg_step) * seg_elems
-// and holds nch chunks of K positions.  Positions are laid out as
-// [position / VEC][lane][VEC], so a lane reads VEC consecutive positions with
-// one 16-byte load.  stg: S * K * 32 elements (16-byte aligned); bars: S
-// mbarriers (8-byte aligned).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Warp-specialised bulk-copy rings.  Each consumer warp owns a ring of S
+// stages of K positions (one 8 KB chunk each) in shared memory, with a "full"
+// mbarrier per stage (completed by the bulk copy's byte count) and an "empty"
+// mbarrier per stage (32 arrivals: every lane of the consumer).  One producer
+// thread issues the copies of all the block's rings, so the consumers never
+// execute a copy instruction.  A ring streams a sequence of equal-length
+// segments (one per tile its consumer processes): segment k starts at
+// src + (seg0 + k * seg_step) * seg_elems and holds nch chunks.  Positions are
+// laid out as [position / VEC][lane][VEC], so a lane reads VEC consecutive
+// positions with one 16-byte load.
 //
-// S - 2 chunks are in flight ahead of the current one: entering chunk c
-// refills the stage of chunk c - 2, never that of c - 1, so a consumer may
-// load its next group (possibly from chunk c) before it has used the values
-// it loaded from chunk c - 1.
+// Entering chunk c releases chunk c - 2 (never c - 1), so a consumer may load
+// its next group, possibly from chunk c, before it has used the values it
+// loaded from chunk c - 1; S - 2 chunks are thus in flight ahead of the
+// current one.  All waits are bounded.
 template <typename T, int K, int S>
-struct BulkRing {
+struct RingConsumer {
     static constexpr int VEC = 16 / (int)sizeof(T);
-    static constexpr uint32_t CB = (uint32_t)K * 32u * (uint32_t)sizeof(T);   // bytes per chunk
     static_assert(K % VEC == 0, "chunk must hold whole vectors");
     static_assert(S >= 3, "two stages plus at least one in flight");
     T *stg;
-    uint32_t bar;
-    const T *src;
-    size_t seg_elems;
-    int seg0, seg_step, nch;
-    int total, issued, pk, pl;    // producer: chunks issued, next (segment, chunk)
-    int ch, off, lane;            // consumer: current chunk and position in it
-    int waited;                   // chunks [0, waited) have completed
+    uint32_t full, empty;
+    int ch, off, lane;
     bool failed;                  // a wait gave up; later takes return stale data
     const T *cur;
 
-    __device__ __forceinline__ void issue() {
-        const int s = issued % S;
-        if (lane == 0) {
-            const T *g = src + (size_t)(seg0 + pk * seg_step) * seg_elems + (size_t)pl * K * 32;
-            mbar_expect_tx(bar + 8u * s, CB);
-            bulk_copy_g2s(smem_addr(stg + (size_t)s * K * 32), g, CB, bar + 8u * s);
-        }
-        if (++pl == nch) {
-            pl = 0;
-            ++pk;
-        }
-        ++issued;
-    }
-    // Barriers are initialised by lane 0; the first S-2 chunks are issued
-    // (now, or by prime() when the source may not be read yet).
-    __device__ __forceinline__ void start(T *stg_, uint64_t *bars, const T *src_, size_t seg_elems_, int seg0_,
-                                          int seg_step_, int nseg, int nch_, int lane_, bool issue_now = true) {
+    __device__ __forceinline__ void start(T *stg_, uint32_t full_, uint32_t empty_, int lane_) {
         stg = stg_;
-        bar = smem_addr(bars);
-        src = src_;
-        seg_elems = seg_elems_;
-        seg0 = seg0_;
-        seg_step = seg_step_;
-        nch = nch_;
-        total = nseg * nch_;
-        issued = 0;
-        pk = 0;
-        pl = 0;
+        full = full_;
+        empty = empty_;
+        lane = lane_;
         ch = -1;
         off = K;
-        lane = lane_;
-        waited = 0;
         failed = false;
         cur = stg + lane * VEC;
-        if (lane == 0) {
-#pragma unroll
-            for (int s = 0; s < S; ++s) mbar_init(bar + 8u * s, 1);
-            mbar_init_fence();
-        }
-        __syncwarp();
-        if (issue_now) prime();
     }
-    __device__ __forceinline__ void prime() {
-        for (int c = 0; c < S - 2 && issued < total; ++c) issue();
-    }
-    // Make chunk c current (waiting for it) and refill the stage of c - 2.
     __device__ __forceinline__ void enter(int c) {
         if (failed) return;
         const int s = c % S;
-        if (!mbar_wait_bounded(bar + 8u * s, (uint32_t)(c / S) & 1u)) {
+        if (!mbar_wait_bounded(full + 8u * s, (uint32_t)(c / S) & 1u)) {
             failed = true;
             return;
         }
-        waited = c + 1;
-        __syncwarp();
-        if (issued < total) issue();
+        if (c >= 2) mbar_arrive(empty + 8u * ((c - 2) % S));
         cur = stg + (size_t)s * K * 32 + lane * VEC;
     }
     // The next G positions (G a multiple of VEC, G <= K) as one group; groups
@@ -255,11 +219,59 @@ struct BulkRing {
     }
     // The current segment is done: the next take starts the next chunk.
     __device__ __forceinline__ void end_segment() { off = K; }
-    // After a failed wait: wait (bounded) for the copies still in flight, so
-    // that none lands after the kernel has returned.
+};
+
+// Producer side, one thread, for up to NC rings of one block.  stg[w], full[w],
+// empty[w]: ring w's stages and barriers; seg0[w] / nseg[w]: its first segment
+// and number of segments.  Issues chunk c of every ring in turn once the
+// ring's consumer has released chunk c - S.  The first `first` chunks of each
+// ring may be issued before the caller's grid-dependency wait (issue_upto),
+// the rest after (run).  At the end it waits for every copy it issued, so none
+// is in flight when its block exits.  Returns false if a wait gave up.
+template <typename T, int K, int S, int NC>
+struct RingProducer {
+    static constexpr uint32_t CB = (uint32_t)K * 32u * (uint32_t)sizeof(T);
+    T *stg[NC];
+    uint32_t full[NC], empty[NC];
+    const T *src;
+    size_t seg_elems;
+    int seg0[NC], nseg[NC], issued[NC], pk[NC], pl[NC];
+    int nc, seg_step, nch, maxc;
+
+    __device__ __forceinline__ bool issue_upto(int cmax) {
+        for (int c = issued_min(); c < cmax; ++c) {
+#pragma unroll
+            for (int w = 0; w < NC; ++w) {
+                if (w >= nc || c >= nseg[w] * nch || c < issued[w]) continue;
+                const int s = c % S;
+                if (c >= S && !mbar_wait_bounded(empty[w] + 8u * s, (uint32_t)(c / S - 1) & 1u)) return false;
+                const T *g = src + (size_t)(seg0[w] + pk[w] * seg_step) * seg_elems + (size_t)pl[w] * K * 32;
+                mbar_expect_tx(full[w] + 8u * s, CB);
+                bulk_copy_g2s(smem_addr(stg[w] + (size_t)s * K * 32), g, CB, full[w] + 8u * s);
+                if (++pl[w] == nch) {
+                    pl[w] = 0;
+                    ++pk[w];
+                }
+                issued[w] = c + 1;
+            }
+        }
+        return true;
+    }
+    __device__ __forceinline__ int issued_min() const {
+        int m = 1 << 30;
+#pragma unroll
+        for (int w = 0; w < NC; ++w)
+            if (w < nc && issued[w] < nseg[w] * nch) m = min(m, issued[w]);
+        return m == (1 << 30) ? maxc : m;
+    }
+    __device__ __forceinline__ bool run() { return issue_upto(maxc); }
     __device__ __forceinline__ void drain() {
-        for (int c = waited; c < issued; ++c)
-            if (!mbar_wait_bounded(bar + 8u * (c % S), (uint32_t)(c / S) & 1u)) return;
+#pragma unroll
+        for (int w = 0; w < NC; ++w) {
+            if (w >= nc) continue;
+            for (int c = max(0, issued[w] - S); c < issued[w]; ++c)
+                if (!mbar_wait_bounded(full[w] + 8u * (c % S), (uint32_t)(c / S) & 1u)) return;
+        }
     }
 };
 
