@@ -1,4 +1,6 @@
 """Helpers shared by the GPU parity tests."""
+import functools
+
 import numpy as np
 
 import oracle
@@ -29,6 +31,12 @@ SMALL = {
 
 def workload(name):
     return inputs.make_workload(**SMALL[name])
+
+
+@functools.lru_cache(maxsize=3)
+def full(name):
+    """A full-size named workload, generated once per test session."""
+    return inputs.named_workload(name)
 
 
 def dev(a):

@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2403_09198_gb300 import inputs
 from paper_2403_09198_gb300.binding import StsError, StsJacobian
-from tests._gpu import (SMALL, TOL64, dev, from_component_major, host, oracle_jac, rel_err,
+from tests._gpu import (SMALL, TOL64, dev, from_component_major, full, host, oracle_jac, rel_err,
                         sol_err, to_component_major, workload)
 
 pytestmark = pytest.mark.gpu
@@ -85,9 +85,9 @@ def _sample_rows(w, rng, n_rand=3000):
     return np.unique(np.array(rows, dtype=np.int64))
 
 
-@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200"])
+@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60"])
 def test_matvec_full_size_sampled(name):
-    w = inputs.named_workload(name)
+    w = full(name)
     J = oracle_jac(w)
     jac = _jac(w, transpose=(name == "grid128_N60"), layout="component")
     rng = np.random.default_rng(11)
@@ -118,20 +118,40 @@ def test_bjacobi_small(name):
     jac.close()
 
 
-def test_bjacobi_full_size_sampled():
-    w = inputs.named_workload("grid128_N60")
+def _sample_cells(w, rng):
+    """First and last cells of the first tiles, of every 97th tile and of the
+    last tile, plus 300 random cells."""
+    nc = w.n_cells
+    ends = [c for t in list(range(0, (nc + 31) // 32, 97)) + [0, 1, 2, (nc - 1) // 32]
+            for c in (32 * t, min(32 * t + 31, nc - 1))]
+    return np.unique(np.concatenate([ends, rng.choice(nc, 300, replace=False)]))
+
+
+@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60"])
+def test_bjacobi_full_size_sampled(name):
+    """Full-size workloads on sampled cells.  On 256 x 256 and 512 x 512 cells
+    each apply warp streams several tiles in a row (its ring runs on across
+    tiles and it copies the next tile's x during the tail), which no small
+    workload does; 512 x 512 also checks the FP32 apply at full size."""
+    w = full(name)
     J = oracle_jac(w)
-    jac = _jac(w, transpose=True, layout="component")
+    big = name == "grid512_N60"
+    jac = _jac(w, transpose=not big, mixed=big, layout="component")
     jac.bjacobi_setup()
     rng = np.random.default_rng(12)
     x = rng.standard_normal(w.n)
-    cells = np.unique(np.concatenate([[0, 127, w.n_cells - 1], rng.choice(w.n_cells, 300, replace=False)]))
+    cells = _sample_cells(w, rng)
     xi = dev(to_component_major(x, w.n_cells, w.b))
-    for trans in (False, True):
+    for trans in ((False,) if big else (False, True)):
         z = from_component_major(host(jac.bjacobi_apply(xi, trans=trans)), w.n_cells, w.b)
         ref = oracle.bj_cells(J, x, cells, trans=trans)
         got = z.reshape(w.n_cells, w.b)[cells]
         assert rel_err(got, ref) <= TOL64, trans
+    if big:
+        z32 = host(jac.bjacobi_apply(xi.float())).astype(np.float64)
+        got = from_component_major(z32, w.n_cells, w.b).reshape(w.n_cells, w.b)[cells]
+        ref = oracle.bj_cells(J, x, cells)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
     jac.close()
 
 
