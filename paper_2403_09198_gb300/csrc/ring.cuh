@@ -88,19 +88,6 @@ struct Ring {
         }
         return cur[(off++) * 32];
     }
-    // The next `width` positions as one row (width <= K): rows never straddle
-    // a chunk, the producer pads a chunk with zeros where the next row would
-    // not fit.  Returns the lane's pointer to the row's first value.
-    __device__ __forceinline__ const T *take(int width) {
-        if (off + width > K) {
-            ++ch;
-            off = 0;
-            enter(ch);
-        }
-        const T *p = cur + off * 32;
-        off += width;
-        return p;
-    }
     __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
 };
 
