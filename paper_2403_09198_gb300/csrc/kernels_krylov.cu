@@ -39,29 +39,59 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 // partial[blk * ld + i0 + i] = sum over this block's elements of V_{i0+i} . w,
-// for i < cnt (cnt <= kDotChunk).  With self = 1 the last slot holds w . w.
-__global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long n, int i0, int cnt,
-                                                      const double *w, double *partial, int ld,
-                                                      int self) {
+// for i < CNT (CNT <= kDotChunk).  With SELF the next slot holds w . w.  The
+// count is a template parameter: a predicated-off FP64 FMA still occupies the
+// FP64 pipe, so the loop must issue exactly CNT (+ SELF) FMAs per element.
+template <int CNT, bool SELF>
+__global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long n, int i0,
+                                                      const double *w, double *partial, int ld) {
     __shared__ double sh[kRedThreads / 32];
-    double acc[kDotChunk + 1];
+    double acc[CNT + 1];
 #pragma unroll
-    for (int i = 0; i <= kDotChunk; ++i) acc[i] = 0.0;
+    for (int i = 0; i <= CNT; ++i) acc[i] = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         const double we = w[e];
 #pragma unroll
-        for (int i = 0; i < kDotChunk; ++i)
-            if (i < cnt) acc[i] = fma(V[(size_t)(i0 + i) * n + e], we, acc[i]);
-        if (self) acc[kDotChunk] = fma(we, we, acc[kDotChunk]);
+        for (int i = 0; i < CNT; ++i) acc[i] = fma(V[(size_t)(i0 + i) * n + e], we, acc[i]);
+        if (SELF) acc[CNT] = fma(we, we, acc[CNT]);
     }
-    for (int i = 0; i < cnt; ++i) {
+#pragma unroll
+    for (int i = 0; i < CNT + (SELF ? 1 : 0); ++i) {
         const double s = block_sum(acc[i], sh);
         if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + i] = s;
     }
-    if (self) {
-        const double s = block_sum(acc[kDotChunk], sh);
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + cnt] = s;
+}
+
+template <int CNT>
+void mdot_launch(const double *V, long long n, int i0, const double *w, double *partial, int ld, bool self,
+                 cudaStream_t st) {
+    if (self) k_mdot<CNT, true><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld);
+    else k_mdot<CNT, false><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld);
+}
+
+// cnt in 0..kDotChunk (cnt = 0 only with self: w . w alone)
+void mdot_dispatch(int cnt, const double *V, long long n, int i0, const double *w, double *partial, int ld,
+                   bool self, cudaStream_t st) {
+    static_assert(kDotChunk == 16, "one case per count");
+    switch (cnt) {
+        case 0: mdot_launch<0>(V, n, i0, w, partial, ld, self, st); break;
+        case 1: mdot_launch<1>(V, n, i0, w, partial, ld, self, st); break;
+        case 2: mdot_launch<2>(V, n, i0, w, partial, ld, self, st); break;
+        case 3: mdot_launch<3>(V, n, i0, w, partial, ld, self, st); break;
+        case 4: mdot_launch<4>(V, n, i0, w, partial, ld, self, st); break;
+        case 5: mdot_launch<5>(V, n, i0, w, partial, ld, self, st); break;
+        case 6: mdot_launch<6>(V, n, i0, w, partial, ld, self, st); break;
+        case 7: mdot_launch<7>(V, n, i0, w, partial, ld, self, st); break;
+        case 8: mdot_launch<8>(V, n, i0, w, partial, ld, self, st); break;
+        case 9: mdot_launch<9>(V, n, i0, w, partial, ld, self, st); break;
+        case 10: mdot_launch<10>(V, n, i0, w, partial, ld, self, st); break;
+        case 11: mdot_launch<11>(V, n, i0, w, partial, ld, self, st); break;
+        case 12: mdot_launch<12>(V, n, i0, w, partial, ld, self, st); break;
+        case 13: mdot_launch<13>(V, n, i0, w, partial, ld, self, st); break;
+        case 14: mdot_launch<14>(V, n, i0, w, partial, ld, self, st); break;
+        case 15: mdot_launch<15>(V, n, i0, w, partial, ld, self, st); break;
+        default: mdot_launch<16>(V, n, i0, w, partial, ld, self, st); break;
     }
 }
 
@@ -180,7 +210,7 @@ struct Red {
         for (int i0 = 0; i0 < k; i0 += kDotChunk) {
             const int cnt = std::min(kDotChunk, k - i0);
             const int sf = self && (i0 + cnt == k);
-            k_mdot<<<kRedBlocks, kRedThreads, 0, h->stream>>>(V, n, i0, cnt, w, K.partial, ld, sf);
+            mdot_dispatch(cnt, V, n, i0, w, K.partial, ld, sf != 0, h->stream);
             STS_LAUNCHED();
         }
         k_reduce<<<k + (self ? 1 : 0), kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, ld, k + (self ? 1 : 0), out);
