@@ -485,6 +485,14 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
     h->ncp = h->n_tiles * kTile;
     h->has_T = d->enable_transpose != 0;
     h->stream = static_cast<cudaStream_t>(d->stream);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->nsm < 1) {
+            delete h;
+            return set_error(STS_ERR_CUDA, "sts_jac_create: cannot query the device");
+        }
+    }
     h->bptr.assign(d->block_indptr, d->block_indptr + nc + 1);
     h->bidx.assign(d->block_indices, d->block_indices + nnzb);
     h->dptr.assign(d->d_indptr, d->d_indptr + b + 1);

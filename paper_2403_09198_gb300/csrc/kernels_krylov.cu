@@ -11,7 +11,7 @@
 // FP32; the basis, the orthogonalisation, x and the residual refresh stay FP64.
 //
 // All reductions are deterministic: a fixed grid writes per-block partial sums
-// in a fixed order and one block adds them in a fixed order.
+// and the block that finishes last adds them in a fixed order.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -38,13 +38,37 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return s;
 }
 
+// The block that finishes last adds the per-block partial sums of `cnt`
+// outputs (partial[b * ld + o], o = o0 .. o0 + cnt - 1) into out[o]: thread t
+// adds blocks t, t + 256, ... and a fixed tree adds the threads, so the order
+// of additions never depends on which block is last or on scheduling.  The
+// ticket counts finished blocks and is reset for the next launch.
+__device__ __forceinline__ void last_block_reduce(double *partial, int ld, int o0, int cnt, double *out,
+                                                  unsigned int *ticket, double *sh) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int o = o0; o < o0 + cnt; ++o) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(partial + (size_t)b * ld + o);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) out[o] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // partial[blk * ld + i0 + i] = sum over this block's elements of V_{i0+i} . w,
 // for i < CNT (CNT <= kDotChunk).  With SELF the next slot holds w . w.  The
 // count is a template parameter: a predicated-off FP64 FMA still occupies the
 // FP64 pipe, so the loop must issue exactly CNT (+ SELF) FMAs per element.
 template <int CNT, bool SELF>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long n, int i0,
-                                                      const double *w, double *partial, int ld) {
+                                                      const double *w, double *partial, int ld, double *out,
+                                                      unsigned int *ticket) {
     __shared__ double sh[kRedThreads / 32];
     double acc[CNT + 1];
 #pragma unroll
@@ -61,63 +85,52 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long
         const double s = block_sum(acc[i], sh);
         if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + i] = s;
     }
+    last_block_reduce(partial, ld, i0, CNT + (SELF ? 1 : 0), out, ticket, sh);
 }
 
 template <int CNT>
 void mdot_launch(const double *V, long long n, int i0, const double *w, double *partial, int ld, bool self,
-                 cudaStream_t st) {
-    if (self) k_mdot<CNT, true><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld);
-    else k_mdot<CNT, false><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld);
+                 double *out, unsigned int *ticket, cudaStream_t st) {
+    if (self) k_mdot<CNT, true><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld, out, ticket);
+    else k_mdot<CNT, false><<<kRedBlocks, kRedThreads, 0, st>>>(V, n, i0, w, partial, ld, out, ticket);
 }
 
 // cnt in 0..kDotChunk (cnt = 0 only with self: w . w alone)
 void mdot_dispatch(int cnt, const double *V, long long n, int i0, const double *w, double *partial, int ld,
-                   bool self, cudaStream_t st) {
+                   bool self, double *out, unsigned int *ticket, cudaStream_t st) {
     static_assert(kDotChunk == 16, "one case per count");
     switch (cnt) {
-        case 0: mdot_launch<0>(V, n, i0, w, partial, ld, self, st); break;
-        case 1: mdot_launch<1>(V, n, i0, w, partial, ld, self, st); break;
-        case 2: mdot_launch<2>(V, n, i0, w, partial, ld, self, st); break;
-        case 3: mdot_launch<3>(V, n, i0, w, partial, ld, self, st); break;
-        case 4: mdot_launch<4>(V, n, i0, w, partial, ld, self, st); break;
-        case 5: mdot_launch<5>(V, n, i0, w, partial, ld, self, st); break;
-        case 6: mdot_launch<6>(V, n, i0, w, partial, ld, self, st); break;
-        case 7: mdot_launch<7>(V, n, i0, w, partial, ld, self, st); break;
-        case 8: mdot_launch<8>(V, n, i0, w, partial, ld, self, st); break;
-        case 9: mdot_launch<9>(V, n, i0, w, partial, ld, self, st); break;
-        case 10: mdot_launch<10>(V, n, i0, w, partial, ld, self, st); break;
-        case 11: mdot_launch<11>(V, n, i0, w, partial, ld, self, st); break;
-        case 12: mdot_launch<12>(V, n, i0, w, partial, ld, self, st); break;
-        case 13: mdot_launch<13>(V, n, i0, w, partial, ld, self, st); break;
-        case 14: mdot_launch<14>(V, n, i0, w, partial, ld, self, st); break;
-        case 15: mdot_launch<15>(V, n, i0, w, partial, ld, self, st); break;
-        default: mdot_launch<16>(V, n, i0, w, partial, ld, self, st); break;
+        case 0: mdot_launch<0>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 1: mdot_launch<1>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 2: mdot_launch<2>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 3: mdot_launch<3>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 4: mdot_launch<4>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 5: mdot_launch<5>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 6: mdot_launch<6>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 7: mdot_launch<7>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 8: mdot_launch<8>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 9: mdot_launch<9>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 10: mdot_launch<10>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 11: mdot_launch<11>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 12: mdot_launch<12>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 13: mdot_launch<13>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 14: mdot_launch<14>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        case 15: mdot_launch<15>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
+        default: mdot_launch<16>(V, n, i0, w, partial, ld, self, out, ticket, st); break;
     }
 }
 
-// out[i] = sum_b partial[b * ld + i]: one block per output; thread t adds
-// partials t, t + 256, ... and a fixed tree adds the threads, so the order of
-// additions never depends on scheduling.
-__global__ void __launch_bounds__(kRedThreads) k_reduce(const double *partial, int nblk, int ld, int cnt,
-                                                        double *out) {
-    __shared__ double sh[kRedThreads / 32];
-    const int i = blockIdx.x;
-    if (i >= cnt) return;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(size_t)b * ld + i];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[i] = s;
-}
-
-// w -= sum_{i<k} h_i V_i; with norm = 1 also partial[blk] = sum w^2 after the update.
+// w -= sum_{i<k} h_i V_i; with norm = 1 also out[0] = ||w||^2 after the update
+// (accumulated in the same sweep, reduced by the last block).
 __global__ void __launch_bounds__(kRedThreads) k_update(double *w, const double *V, long long n,
                                                         const double *hcoef, int k, double *partial,
-                                                        int norm) {
+                                                        int norm, double *out, unsigned int *ticket) {
     __shared__ double sh[kRedThreads / 32];
     __shared__ double hs[64];
     double acc = 0.0;
     for (int i0 = 0; i0 < k; i0 += 64) {
         const int cnt = min(64, k - i0);
+        const bool last_chunk = i0 + 64 >= k;
         __syncthreads();
         if (threadIdx.x < cnt) hs[threadIdx.x] = hcoef[i0 + threadIdx.x];
         __syncthreads();
@@ -126,18 +139,18 @@ __global__ void __launch_bounds__(kRedThreads) k_update(double *w, const double 
             double v = w[e];
             for (int i = 0; i < cnt; ++i) v = fma(-hs[i], V[(size_t)(i0 + i) * n + e], v);
             w[e] = v;
+            if (norm && last_chunk) acc = fma(v, v, acc);
         }
     }
     if (norm) {
-        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-             e += (long long)gridDim.x * blockDim.x)
-            acc = fma(w[e], w[e], acc);
         const double s = block_sum(acc, sh);
         if (threadIdx.x == 0) partial[blockIdx.x] = s;
+        last_block_reduce(partial, 1, 0, 1, out, ticket, sh);
     }
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_norm2(const double *v, long long n, double *partial) {
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const double *v, long long n, double *partial, double *out,
+                                                       unsigned int *ticket) {
     __shared__ double sh[kRedThreads / 32];
     double acc = 0.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -145,6 +158,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const double *v, long lon
         acc = fma(v[e], v[e], acc);
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    last_block_reduce(partial, 1, 0, 1, out, ticket, sh);
 }
 
 __global__ void k_sub(double *r, const double *b, const double *y, long long n) {
@@ -203,35 +217,28 @@ sts_status opM64(sts_jac_s *h, int dir, const double *x, double *z) {
 struct Red {
     sts_jac_s *h;
     long long n;
-    // device: partial [kRedBlocks][ld], reduced values land in h->kry.red
+    // device: per-block partials in h->kry.partial, totals written by each
+    // kernel's last block (h->kry.ticket)
     sts_status dots(const double *V, int k, const double *w, int self, double *out) {
         Krylov &K = h->kry;
         const int ld = K.m + 2;
         for (int i0 = 0; i0 < k; i0 += kDotChunk) {
             const int cnt = std::min(kDotChunk, k - i0);
             const int sf = self && (i0 + cnt == k);
-            mdot_dispatch(cnt, V, n, i0, w, K.partial, ld, sf != 0, h->stream);
+            mdot_dispatch(cnt, V, n, i0, w, K.partial, ld, sf != 0, out, K.ticket, h->stream);
             STS_LAUNCHED();
         }
-        k_reduce<<<k + (self ? 1 : 0), kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, ld, k + (self ? 1 : 0), out);
-        STS_LAUNCHED();
         return STS_OK;
     }
     sts_status update(double *w, const double *V, int k, const double *hcoef, int norm, double *out) {
         Krylov &K = h->kry;
-        k_update<<<kRedBlocks, kRedThreads, 0, h->stream>>>(w, V, n, hcoef, k, K.partial, norm);
+        k_update<<<kRedBlocks, kRedThreads, 0, h->stream>>>(w, V, n, hcoef, k, K.partial, norm, out, K.ticket);
         STS_LAUNCHED();
-        if (norm) {
-            k_reduce<<<1, kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
-            STS_LAUNCHED();
-        }
         return STS_OK;
     }
     sts_status norm2(const double *v, double *out) {
         Krylov &K = h->kry;
-        k_norm2<<<kRedBlocks, kRedThreads, 0, h->stream>>>(v, n, K.partial);
-        STS_LAUNCHED();
-        k_reduce<<<1, kRedThreads, 0, h->stream>>>(K.partial, kRedBlocks, 1, 1, out);
+        k_norm2<<<kRedBlocks, kRedThreads, 0, h->stream>>>(v, n, K.partial, out, K.ticket);
         STS_LAUNCHED();
         return STS_OK;
     }
@@ -247,6 +254,10 @@ sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
         K.Z32 = nullptr;
         STS_TRY(dalloc(h, &K.partial, (size_t)kRedBlocks * (m + 2)));
         STS_TRY(dalloc(h, &K.red, (size_t)3 * (m + 2)));
+        if (!K.ticket) {
+            STS_TRY(dalloc(h, &K.ticket, 1));
+            STS_CK(cudaMemsetAsync(K.ticket, 0, sizeof(unsigned int), h->stream));
+        }
         if (!K.w) {
             STS_TRY(dalloc(h, &K.w, n));
             STS_TRY(dalloc(h, &K.r, n));

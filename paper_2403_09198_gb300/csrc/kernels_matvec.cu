@@ -514,13 +514,16 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
             case 3: kern = creg ? k_mv_struct<T, 3, true> : k_mv_struct<T, 3, false>; break;
             default: kern = creg ? k_mv_struct<T, 4, true> : k_mv_struct<T, 4, false>; break;
         }
-        if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0, dev = 0, nsm = 0;
-        STS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * kTile, smem));
-        STS_CK(cudaGetDevice(&dev));
-        STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int &resident = h->mvs_blocks[sizeof(T) == 8 ? 0 : 1];    // blocks resident at once, found once
+        if (!resident) {
+            if (smem > 48 * 1024)
+                STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            STS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * kTile, smem));
+            resident = std::max(per_sm, 1) * h->nsm;
+        }
         const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        const long long blocks = std::max(1LL, std::min(need, (long long)std::max(per_sm, 1) * nsm));
+        const long long blocks = std::max(1LL, std::min(need, (long long)resident));
         // an ordinary launch: with a programmatic early start the persistent
         // blocks begin at different times during pass 1 and finish unevenly
         kern<<<(unsigned)blocks, kWarpsPerBlock * kTile, smem, h->stream>>>(a);

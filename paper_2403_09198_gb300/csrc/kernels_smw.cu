@@ -1102,11 +1102,11 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
         case 3: kern = r2 ? k_smw_sapply<T, 3, 2> : k_smw_sapply<T, 3, 4>; break;
         default: kern = r2 ? k_smw_sapply<T, 4, 2> : k_smw_sapply<T, 4, 4>; break;
     }
-    if (smem > 48 * 1024) STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, nsm = 0;
-    STS_CK(cudaGetDevice(&dev));
-    STS_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = std::max(1, std::min(nsm, (h->n_tiles + wpb - 1) / wpb));
+    bool &attr = h->sap_attr[sizeof(T) == 8 ? 0 : 1];
+    if (!attr && smem > 48 * 1024)
+        STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+    const int blocks = std::max(1, std::min(h->nsm, (h->n_tiles + wpb - 1) / wpb));
     STS_CK(launch_pdl(kern, dim3(blocks), dim3((wpb + 1) * kTile), smem, h->stream, a));
     STS_LAUNCHED();
     h->streams_dirty = false;

@@ -225,7 +225,8 @@ struct Krylov {
     float *t32a = nullptr, *t32b = nullptr;   // [n]
     double *w = nullptr, *r = nullptr, *xb = nullptr, *bb = nullptr, *tmp = nullptr;  // [n]
     double *partial = nullptr;   // [kRedBlocks][m+2]
-    double *red = nullptr;       // [m+2]
+    double *red = nullptr;       // [3][m+2] reduced dots and norms
+    unsigned int *ticket = nullptr;   // finished-block counter of the last-block reductions (0 between launches)
     double *h_pinned = nullptr;  // host pinned [m+2]
     double *c = nullptr;         // pair dots scratch [n_tiles*n_pslots*32]
     float *c32 = nullptr;
@@ -245,6 +246,10 @@ struct sts_jac_s {
     // update or block-Jacobi setup): the next hot kernel must not read them
     // before its grid-dependency wait.
     bool streams_dirty = true;
+    // launch data computed on first use (per precision: 0 FP64, 1 FP32)
+    int nsm = 0;                        // SMs of the handle's device
+    int mvs_blocks[2] = {0, 0};         // grid of the structured pass 2
+    bool sap_attr[2] = {false, false};  // shared-memory limit of the structured apply set
     // host copies of the structure
     std::vector<int> bptr, bidx, dptr, didx, optr, oidx;
     std::vector<long long> soff;    // [nnzb+1]
