@@ -619,12 +619,14 @@ const char *sts_last_error(void) { return g_err; }
 const char *sts_version(void) { return "sts-gb300 1.0 (sm_103a)"; }
 
 sts_status sts_jac_create(const sts_jac_desc *desc, sts_jac_t *out) {
+    NvtxRange nvtx_range("sts_jac_create");
     g_err[0] = 0;
     STS_GUARD(return create_impl(desc, out);)
 }
 
 sts_status sts_jac_update_values(sts_jac_t h, const double *S, const double *U, const double *V,
                                  int values_on_host) {
+    NvtxRange nvtx_range("sts_jac_update_values");
     if (!h) return set_error(STS_ERR_INVALID_ARG, "sts_jac_update_values: handle is NULL");
     if (!S || (h->n_pairs > 0 && (!U || !V)))
         return set_error(STS_ERR_INVALID_ARG, "sts_jac_update_values: NULL value array");
@@ -632,6 +634,7 @@ sts_status sts_jac_update_values(sts_jac_t h, const double *S, const double *U, 
 }
 
 sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans) {
+    NvtxRange nvtx_range("sts_jac_matvec");
     STS_TRY(check_handle(h, x, y, "sts_jac_matvec"));
     if (trans && (!h->has_T || h->rep != STS_REP_FACTORED))
         return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec: trans = 1 needs a factored handle with enable_transpose");
@@ -642,6 +645,7 @@ sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans) {
 }
 
 sts_status sts_jac_matvec_noalloc(sts_jac_t h, const double *x, double *y, int trans) {
+    NvtxRange nvtx_range("sts_jac_matvec_noalloc");
     STS_TRY(check_handle(h, x, y, "sts_jac_matvec_noalloc"));
     if (h->rep != STS_REP_FACTORED)
         return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_noalloc: needs the factored representation");
@@ -654,6 +658,7 @@ sts_status sts_jac_matvec_noalloc(sts_jac_t h, const double *x, double *y, int t
 }
 
 sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans) {
+    NvtxRange nvtx_range("sts_jac_matvec_f32");
     STS_TRY(check_handle(h, x, y, "sts_jac_matvec_f32"));
     if (h->dtype != STS_MIXED) return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_f32: handle has no FP32 operators");
     if (trans && !h->has_T) return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_f32: no transposed operators");
@@ -664,12 +669,14 @@ sts_status sts_jac_matvec_f32(sts_jac_t h, const float *x, float *y, int trans) 
 }
 
 sts_status sts_jac_bjacobi_setup(sts_jac_t h) {
+    NvtxRange nvtx_range("sts_jac_bjacobi_setup");
     if (!h) return set_error(STS_ERR_INVALID_ARG, "sts_jac_bjacobi_setup: handle is NULL");
     STS_GUARD(STS_TRY(check_device(h));
               return h->rep == STS_REP_FACTORED ? smw_setup(h) : dense_setup(h);)
 }
 
 sts_status sts_jac_bjacobi_apply(sts_jac_t h, const double *x, double *z, int trans) {
+    NvtxRange nvtx_range("sts_jac_bjacobi_apply");
     STS_TRY(check_handle(h, x, z, "sts_jac_bjacobi_apply"));
     const bool ready = h->rep == STS_REP_FACTORED ? h->smw.ready : h->dense.ready;
     if (!ready) return set_error(STS_ERR_NOT_SETUP, "sts_jac_bjacobi_apply: call sts_jac_bjacobi_setup first");
@@ -682,6 +689,7 @@ sts_status sts_jac_bjacobi_apply(sts_jac_t h, const double *x, double *z, int tr
 }
 
 sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int trans) {
+    NvtxRange nvtx_range("sts_jac_bjacobi_apply_f32");
     STS_TRY(check_handle(h, x, z, "sts_jac_bjacobi_apply_f32"));
     if (h->dtype != STS_MIXED) return set_error(STS_ERR_INVALID_ARG, "sts_jac_bjacobi_apply_f32: handle has no FP32 operators");
     if (!h->smw.ready) return set_error(STS_ERR_NOT_SETUP, "sts_jac_bjacobi_apply_f32: call sts_jac_bjacobi_setup first");
@@ -694,6 +702,7 @@ sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int 
 
 sts_status sts_gmres_solve(sts_jac_t h, const double *b, double *x, const sts_gmres_opts *opts,
                            sts_gmres_info *info) {
+    NvtxRange nvtx_range("sts_gmres_solve");
     STS_TRY(check_handle(h, b, x, "sts_gmres_solve"));
     STS_GUARD(const sts_status st = gmres(h, b, x, opts, info);
               if (st == STS_OK || st == STS_ERR_NOT_CONVERGED || st == STS_ERR_NUMERIC) STS_TRY(check_device(h));
@@ -701,6 +710,7 @@ sts_status sts_gmres_solve(sts_jac_t h, const double *b, double *x, const sts_gm
 }
 
 sts_status sts_jac_grad(sts_jac_t h, const double *lambda, const double *x, double *gS, double *gU, double *gV) {
+    NvtxRange nvtx_range("sts_jac_grad");
     STS_TRY(check_handle(h, lambda, x, "sts_jac_grad"));
     if (!gS || (h->n_pairs > 0 && (!gU || !gV))) return set_error(STS_ERR_INVALID_ARG, "sts_jac_grad: NULL output");
     if (h->rep != STS_REP_FACTORED || !h->has_T)
@@ -709,6 +719,7 @@ sts_status sts_jac_grad(sts_jac_t h, const double *lambda, const double *x, doub
 }
 
 sts_status sts_selftest_bounded_wait(void *stream_) {
+    NvtxRange nvtx_range("sts_selftest_bounded_wait");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     int *d_flag = nullptr, flag = 0;
     if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess)
@@ -740,6 +751,7 @@ sts_status sts_jac_memory(sts_jac_t h, size_t *bytes) {
 }
 
 sts_status sts_jac_destroy(sts_jac_t h) {
+    NvtxRange nvtx_range("sts_jac_destroy");
     if (!h) return STS_OK;
     cudaStreamSynchronize(h->stream);
     free_all(h);

@@ -339,6 +339,7 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
         std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
         int its = 0;
         for (;;) {
+            NvtxRange nvtx_cycle("gmres cycle");
             // true residual r = b - A x
             STS_TRY(opA64(h, dir, K.xb, K.w));
             k_sub<<<nb, 256, 0, h->stream>>>(K.r, K.bb, K.w, n);
@@ -361,6 +362,7 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
             g[0] = beta;
             int k = 0;
             for (int j = 0; j < m; ++j) {
+                NvtxRange nvtx_step("gmres arnoldi step");
                 double *vj = K.V + (size_t)j * n;
                 // z_j = M v_j, w = A z_j
                 if (!mixed) {

@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sts.h"
 
 namespace sts {
@@ -68,6 +70,15 @@ sts_status set_error(sts_status s, const char *fmt, ...);
 extern std::atomic<unsigned long long> g_launches;
 
 // After every kernel launch: count it and surface launch errors.
+// NVTX range for the life of a scope (visible in Nsight timelines; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Launch with programmatic dependent launch allowed: the kernel may start
 // while the previous kernel on the stream finishes, and must call
 // griddepcontrol.wait (pdl_wait) before it reads anything an earlier kernel
