@@ -54,9 +54,27 @@ template <> struct Chunk<float> { static constexpr int CH = 16; };
 // family, the dense flow rows of S.  Two register buffers alternate so the
 // loads of the next chunk are in flight while the current one is multiplied;
 // the stream is padded to Lp (a multiple of the chunk) with zero coefficients.
+// Pass-1 stream loads: FP32 positions in 16-byte vectors of 4 (the FP32
+// kernel is bound by memory instructions), FP64 one position per load (the
+// FP64 kernel is bound by the FP64 pipe, and measured faster so).
+template <typename T> struct DotVec;
+template <> struct DotVec<double> {
+    using type = double;
+    static constexpr int n = 1;
+};
+template <> struct DotVec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+__device__ __forceinline__ double dot_el(double v, int) { return v; }
+__device__ __forceinline__ float dot_el(const float4 &v, int i) { return vel(v, i); }
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
+    using V = typename DotVec<T>::type;
     constexpr int CH = Chunk<T>::CH;
+    constexpr int VEC = DotVec<T>::n, NV = CH / VEC;
+    static_assert(CH % VEC == 0, "a chunk is whole vectors");
     const int lane = threadIdx.x & 31;
     const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wid >= (long long)a.n_tiles * a.n_dtasks) return;
@@ -64,11 +82,14 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
     const int s = a.dtask_slot[k];
     const bool present = (a.slot_mask[t] >> s) & 1u;
     const int j = present ? a.nbr[((size_t)t * a.n_slots + s) * kTile + lane] : -1;
-    const T *__restrict__ dv = a.dotv + ((size_t)t * a.n_dtasks + k) * a.Lp * kTile + lane;
-    T va[CH], xa[CH], vb[CH], xb[CH];
+    // the task's stream as [Lp / VEC][lane][VEC]: vector p of this lane at dv[p * 32]
+    const V *__restrict__ dv =
+        reinterpret_cast<const V *>(a.dotv + ((size_t)t * a.n_dtasks + k) * a.Lp * kTile) + lane;
+    V va[NV], vb[NV];
+    T xa[CH], xb[CH];
     if (present && a.pre) {
 #pragma unroll
-        for (int i = 0; i < CH; ++i) va[i] = __ldg(dv + (size_t)i * kTile);
+        for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + i * kTile);
     }
     pdl_wait();
     pdl_trigger();
@@ -80,30 +101,28 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
         const size_t ncp = a.ncp;
         if (!a.pre) {
 #pragma unroll
-            for (int i = 0; i < CH; ++i) va[i] = __ldg(dv + (size_t)i * kTile);
+            for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + i * kTile);
         }
 #pragma unroll
         for (int i = 0; i < CH; ++i) xa[i] = __ldg(xj + (size_t)min(i, bm1) * ncp);
         for (int base = 0; base < a.Lp; base += 2 * CH) {
             if (base + CH < a.Lp) {
 #pragma unroll
-                for (int i = 0; i < CH; ++i) {
-                    vb[i] = __ldg(dv + (size_t)(base + CH + i) * kTile);
-                    xb[i] = __ldg(xj + (size_t)min(base + CH + i, bm1) * ncp);
-                }
+                for (int i = 0; i < NV; ++i) vb[i] = __ldg(dv + ((base + CH) / VEC + i) * kTile);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) xb[i] = __ldg(xj + (size_t)min(base + CH + i, bm1) * ncp);
             }
 #pragma unroll
-            for (int i = 0; i < CH; ++i) acc = fma(va[i], xa[i], acc);
+            for (int i = 0; i < CH; ++i) acc = fma(dot_el(va[i / VEC], i % VEC), xa[i], acc);
             if (base + CH >= a.Lp) break;
             if (base + 2 * CH < a.Lp) {
 #pragma unroll
-                for (int i = 0; i < CH; ++i) {
-                    va[i] = __ldg(dv + (size_t)(base + 2 * CH + i) * kTile);
-                    xa[i] = __ldg(xj + (size_t)min(base + 2 * CH + i, bm1) * ncp);
-                }
+                for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + ((base + 2 * CH) / VEC + i) * kTile);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) xa[i] = __ldg(xj + (size_t)min(base + 2 * CH + i, bm1) * ncp);
             }
 #pragma unroll
-            for (int i = 0; i < CH; ++i) acc = fma(vb[i], xb[i], acc);
+            for (int i = 0; i < CH; ++i) acc = fma(dot_el(vb[i / VEC], i % VEC), xb[i], acc);
         }
     }
     a.c[((size_t)t * a.n_dtasks + k) * kTile + lane] = acc;
@@ -360,20 +379,25 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
 // Repack the public values into one stream of one direction.  Each stream
 // position (per tile and lane) is an S entry of a block slot, an entry of a
 // pair vector (the axpy vectors in the main stream, the dot vectors in the
-// pass-1 stream), or a zero.
+// pass-1 stream), or a zero.  With vec > 1 each run of vec positions of a
+// lane is contiguous ([tile][position / vec][lane][vec]), for 16-byte loads.
 template <typename T>
 __global__ void k_repack(T *out, const double *S, const double *AX, const int *blk,
                               const long long *soff, const int *pbase, const int *pos_kind,
                               const int *pos_arg, const int *pat_src, const int *pslot_slot,
                               const int *pslot_local, long long tile_len, int n_tiles, int n_slots,
-                              int b) {
-    const long long total = (long long)n_tiles * tile_len * kTile;
+                              int b, int vec) {
+    const long long per_tile = tile_len * kTile;
+    const long long total = (long long)n_tiles * per_tile;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const int lane = (int)(i % kTile);
-        const long long r = i / kTile;
-        const long long pos = r % tile_len;
-        const int t = (int)(r / tile_len);
+        // element i is (tile, position / vec, lane, position % vec)
+        const int t = (int)(i / per_tile);
+        const long long e = i - (long long)t * per_tile;
+        const long long vb = e / (kTile * vec);
+        const int rem = (int)(e - vb * kTile * vec);
+        const int lane = rem / vec;
+        const long long pos = vb * vec + rem % vec;
         const int kind = pos_kind[pos], arg = pos_arg[pos];
         double v = 0.0;
         if (kind == kPosZero) {
@@ -542,16 +566,19 @@ sts_status mv_repack(sts_jac_s *h, int dir, const double *S, const double *U, co
     const double *DV = dir == 0 ? V : U;   // dot vectors (pass-1 stream)
     const long long nm = (long long)h->n_tiles * P.tile_len * kTile;
     const long long nd = (long long)h->n_tiles * P.n_dtasks * P.Lp * kTile;
-    auto rp = [&](auto *out, const double *vec, const int *pk, const int *pa, long long len, long long total) {
+    auto rp = [&](auto *out, const double *vec, const int *pk, const int *pa, long long len, long long total,
+                  int vw) {
         using T = std::remove_pointer_t<decltype(out)>;
         k_repack<T><<<grid_for(total, 256), 256, 0, h->stream>>>(out, S, vec, P.blk, h->d_soff, h->d_pbase, pk, pa,
                                                                  P.pat_src, P.pslot_slot, P.pslot_local, len,
-                                                                 h->n_tiles, P.n_slots, h->b);
+                                                                 h->n_tiles, P.n_slots, h->b, vw);
     };
-    if (P.main64) { rp(P.main64, AX, P.pos_kind, P.pos_arg, P.tile_len, nm); STS_LAUNCHED(); }
-    if (P.main32) { rp(P.main32, AX, P.pos_kind, P.pos_arg, P.tile_len, nm); STS_LAUNCHED(); }
-    if (nd > 0 && P.dotv64) { rp(P.dotv64, DV, P.dpos_kind, P.dpos_arg, (long long)P.n_dtasks * P.Lp, nd); STS_LAUNCHED(); }
-    if (nd > 0 && P.dotv32) { rp(P.dotv32, DV, P.dpos_kind, P.dpos_arg, (long long)P.n_dtasks * P.Lp, nd); STS_LAUNCHED(); }
+    // the pass-1 stream is read with loads of DotVec<T>::n positions per lane
+    const long long dlen = (long long)P.n_dtasks * P.Lp;
+    if (P.main64) { rp(P.main64, AX, P.pos_kind, P.pos_arg, P.tile_len, nm, 1); STS_LAUNCHED(); }
+    if (P.main32) { rp(P.main32, AX, P.pos_kind, P.pos_arg, P.tile_len, nm, 1); STS_LAUNCHED(); }
+    if (nd > 0 && P.dotv64) { rp(P.dotv64, DV, P.dpos_kind, P.dpos_arg, dlen, nd, DotVec<double>::n); STS_LAUNCHED(); }
+    if (nd > 0 && P.dotv32) { rp(P.dotv32, DV, P.dpos_kind, P.dpos_arg, dlen, nd, DotVec<float>::n); STS_LAUNCHED(); }
     return STS_OK;
 }
 

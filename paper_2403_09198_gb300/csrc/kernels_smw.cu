@@ -345,18 +345,6 @@ __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
     return (raw + 127) / 128 * 128;
 }
 
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<double> {
-    using type = double2;
-};
-template <>
-struct Vec16<float> {
-    using type = float4;
-};
-__device__ __forceinline__ double vel(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
-__device__ __forceinline__ float vel(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
 // One group of G positions in registers (G / VEC 16-byte loads).
 template <typename T, int G>

@@ -100,6 +100,21 @@ struct Ring {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// 16-byte vector of T (2 doubles or 4 floats) and its element i (constant i
+// after unrolling, so no data moves).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+__device__ __forceinline__ double vel(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vel(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
 // ---------------------------------------------------------------------------
 // Bulk copies completed on mbarriers.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
