@@ -307,7 +307,7 @@ def run_ours(args):
         hx = xv.cpu().pin_memory()
         hb = torch.from_numpy(w.rhs).pin_memory()
         hW = torch.from_numpy(w.W).pin_memory()
-        outs = None
+        outs = None            # pinned host buffers for the step's results, made on first use
 
         def e2e_step():
             nonlocal outs
@@ -316,7 +316,11 @@ def run_ours(args):
             b.copy_(hb, non_blocking=True)
             Wd.copy_(hW, non_blocking=True)
             xs, xm, lam, g = step()
-            outs = [y.cpu(), z.cpu(), xs.cpu(), xm.cpu(), lam.cpu()] + [a.cpu() for a in g]
+            res = [y, z, xs, xm, lam] + list(g)
+            if outs is None:
+                outs = [torch.empty(a.shape, dtype=a.dtype, pin_memory=True) for a in res]
+            for o, a in zip(outs, res):
+                o.copy_(a, non_blocking=True)
             return outs
 
         e2e_step()
