@@ -1,13 +1,17 @@
-// ring.cuh -- per-warp shared-memory rings that stream coefficient positions
-// (32 lanes x sizeof(T) bytes each) from global memory ahead of the consumer.
+// ring.cuh -- shared-memory rings that stream coefficient positions (32 lanes
+// x sizeof(T) bytes each) from global memory ahead of the consumer, and the
+// device helpers they use.
 //
-// Ring:     strided positions, copied with cp.async (16 bytes per lane and
-//           instruction); waits are cp.async.wait_group, no spin loop.
-// BulkRing: contiguous chunks copied by the bulk-copy (TMA) engine, one
-//           cp.async.bulk per chunk issued by lane 0 and completed on one
-//           mbarrier per stage; waits are bounded in time.
-// In both, chunk c lives in stage c % S and the warp synchronises before a
-// stage is refilled, so every lane has finished reading it.
+// Ring:         one warp, strided positions copied with cp.async (16 bytes per
+//               lane and instruction); waits are cp.async.wait_group, no spin
+//               loop.  Used by the generic block-Jacobi apply.
+// RingConsumer / RingProducer: contiguous 8 KB chunks copied by the bulk-copy
+//               (TMA) engine, issued by one producer thread for all the rings
+//               of a block and completed on a "full" mbarrier per stage; the
+//               consumer warp releases a stage through an "empty" mbarrier;
+//               every wait is bounded in time.  Used by the structured apply.
+// In all of them chunk c lives in stage c % S and a stage is refilled only
+// after every lane has finished reading it.
 #pragma once
 
 #include <cuda_runtime.h>
