@@ -5,7 +5,8 @@
 //
 // The paper's CPU listing computes pass 1 for one block row and then
 // accumulates that row; here pass 1 runs for all pairs first (one warp per
-// tile and pair slot) and pass 2 runs one warp per (tile, row group).  In both
+// tile and dot task; for the paper's pattern family the dense flow rows of S
+// are dot tasks too) and pass 2 runs one warp per (tile, row group).  In both
 // passes lane = cell, each lane accumulates its own sums serially (one FMA per
 // multiply-add, no cross-lane reduction), and every stream value is read once
 // with a coalesced 32-lane request.  The transposed product J^T x uses the

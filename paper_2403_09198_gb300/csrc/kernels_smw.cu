@@ -298,9 +298,10 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
 // dependency chain is one FMA per row.
 //
 // Stream layout.  Rows are packed in groups of whole 16-byte vectors (VEC =
-// 16 / sizeof(T) positions): a group is the least number of consecutive rows
-// of one section whose width is a multiple of VEC (rows past the end of the
-// section are zero), or one single row padded with zeros.  Groups never
+// 16 / sizeof(T) positions): a group is a run of consecutive rows of one
+// section whose width is a multiple of VEC and at least 16 positions (rows
+// past the end of the section are zero; see sap_group_rows), or one single row
+// padded with zeros.  Groups never
 // straddle a chunk of K positions (8 KB), and each tile's stream is padded to
 // whole chunks, so one tile's stream is Lt contiguous positions stored as
 // [tile][position / VEC][lane][VEC]: a chunk is one bulk copy and a lane reads
@@ -316,7 +317,7 @@ struct SApplyArgs {
     int pre;                // the stream and C^-1 may be read before the grid-dependency wait
 };
 
-constexpr int kApWarps = 4;              // warps per block of the structured apply (one per sub-partition)
+constexpr int kApWarps = 4;              // consumer warps per block of the structured apply (one per sub-partition)
 constexpr int kSApStages = 5;            // ring stages of the structured apply (three chunks in flight)
 constexpr int kSApChunkBytes = 8192;     // bytes per stage (one bulk copy)
 
