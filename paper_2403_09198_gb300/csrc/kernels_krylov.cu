@@ -26,25 +26,35 @@ constexpr int kRedBlocks = 304;     // 2 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kDotChunk = 16;       // vectors per multi-dot sweep
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// Per-block sums of the first NV of the values v at once: every warp reduces
+// them with shuffles, then thread i < NV adds the warps' results in warp order
+// and writes row[i].  One barrier for all NV values.  sh: 8 * NV doubles.
+template <int NV, int NA>
+__device__ __forceinline__ void block_partials(double (&v)[NA], double *row, double *sh) {
+    static_assert(NV <= NA, "values to reduce");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+        if (lane == 0) sh[w * NV + i] = v[i];
+    }
     __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
-    return s;
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k * NV + threadIdx.x];
+        row[threadIdx.x] = s;
+    }
 }
 
 // The block that finishes last adds the per-block partial sums of `cnt`
-// outputs (partial[b * ld + o], o = o0 .. o0 + cnt - 1) into out[o]: thread t
-// adds blocks t, t + 256, ... and a fixed tree adds the threads, so the order
-// of additions never depends on which block is last or on scheduling.  The
-// ticket counts finished blocks and is reset for the next launch.
+// outputs (partial[b * ld + o], o = o0 .. o0 + cnt - 1) into out[o]: warp w
+// takes outputs w, w + 8, ...; lane l adds blocks l, l + 32, ... and the
+// shuffle tree adds the lanes, so the order of additions never depends on
+// which block is last or on scheduling.  The ticket counts finished blocks
+// and is reset for the next launch.
 __device__ __forceinline__ void last_block_reduce(double *partial, int ld, int o0, int cnt, double *out,
-                                                  unsigned int *ticket, double *sh) {
+                                                  unsigned int *ticket) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -52,12 +62,15 @@ __device__ __forceinline__ void last_block_reduce(double *partial, int ld, int o
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int o = o0; o < o0 + cnt; ++o) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = o0 + w; o < o0 + cnt; o += nw) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(partial + (size_t)b * ld + o);
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) out[o] = s;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partial + (size_t)b * ld + o);
+#pragma unroll
+        for (int k = 16; k > 0; k >>= 1) s += __shfl_down_sync(0xffffffffu, s, k);
+        if (lane == 0) out[o] = s;
     }
+    __syncthreads();
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -69,23 +82,39 @@ template <int CNT, bool SELF>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(const double *V, long long n, int i0,
                                                       const double *w, double *partial, int ld, double *out,
                                                       unsigned int *ticket) {
-    __shared__ double sh[kRedThreads / 32];
+    // elements per thread and iteration: all their loads are issued before the
+    // FMAs, so a thread keeps several memory requests in flight
+    constexpr int U = CNT + 1 <= 3 ? 4 : CNT + 1 <= 7 ? 2 : 1;
+    constexpr int NO = CNT + (SELF ? 1 : 0);          // outputs
+    __shared__ double sh[(kRedThreads / 32) * (CNT + 1)];
     double acc[CNT + 1];
 #pragma unroll
     for (int i = 0; i <= CNT; ++i) acc[i] = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e + (U - 1) * stride < n; e += U * stride) {
+        double we[U], vv[U][CNT > 0 ? CNT : 1];
+#pragma unroll
+        for (int u = 0; u < U; ++u) we[u] = w[e + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < CNT; ++i) vv[u][i] = V[(size_t)(i0 + i) * n + e + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int i = 0; i < CNT; ++i) acc[i] = fma(vv[u][i], we[u], acc[i]);
+            if (SELF) acc[CNT] = fma(we[u], we[u], acc[CNT]);
+        }
+    }
+    for (; e < n; e += stride) {
         const double we = w[e];
 #pragma unroll
         for (int i = 0; i < CNT; ++i) acc[i] = fma(V[(size_t)(i0 + i) * n + e], we, acc[i]);
         if (SELF) acc[CNT] = fma(we, we, acc[CNT]);
     }
-#pragma unroll
-    for (int i = 0; i < CNT + (SELF ? 1 : 0); ++i) {
-        const double s = block_sum(acc[i], sh);
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * ld + i0 + i] = s;
-    }
-    last_block_reduce(partial, ld, i0, CNT + (SELF ? 1 : 0), out, ticket, sh);
+    block_partials<NO>(acc, partial + (size_t)blockIdx.x * ld + i0, sh);
+    last_block_reduce(partial, ld, i0, NO, out, ticket);
 }
 
 template <int CNT>
@@ -120,32 +149,78 @@ void mdot_dispatch(int cnt, const double *V, long long n, int i0, const double *
     }
 }
 
-// w -= sum_{i<k} h_i V_i; with norm = 1 also out[0] = ||w||^2 after the update
-// (accumulated in the same sweep, reduced by the last block).
+// w -= sum_{i<CNT} h_{i0+i} V_{i0+i}; with NORM also out[0] = ||w||^2 after the
+// update (accumulated in the same sweep, reduced by the last block).  CNT is a
+// template parameter for the same reason as in k_mdot.
+template <int CNT, bool NORM>
 __global__ void __launch_bounds__(kRedThreads) k_update(double *w, const double *V, long long n,
-                                                        const double *hcoef, int k, double *partial,
-                                                        int norm, double *out, unsigned int *ticket) {
+                                                        const double *hcoef, int i0, double *partial,
+                                                        double *out, unsigned int *ticket) {
+    constexpr int U = CNT + 1 <= 3 ? 4 : CNT + 1 <= 7 ? 2 : 1;
     __shared__ double sh[kRedThreads / 32];
-    __shared__ double hs[64];
+    double h[CNT > 0 ? CNT : 1];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) h[i] = __ldg(hcoef + i0 + i);
     double acc = 0.0;
-    for (int i0 = 0; i0 < k; i0 += 64) {
-        const int cnt = min(64, k - i0);
-        const bool last_chunk = i0 + 64 >= k;
-        __syncthreads();
-        if (threadIdx.x < cnt) hs[threadIdx.x] = hcoef[i0 + threadIdx.x];
-        __syncthreads();
-        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-             e += (long long)gridDim.x * blockDim.x) {
-            double v = w[e];
-            for (int i = 0; i < cnt; ++i) v = fma(-hs[i], V[(size_t)(i0 + i) * n + e], v);
-            w[e] = v;
-            if (norm && last_chunk) acc = fma(v, v, acc);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e + (U - 1) * stride < n; e += U * stride) {
+        double v[U], vv[U][CNT > 0 ? CNT : 1];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = w[e + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < CNT; ++i) vv[u][i] = V[(size_t)(i0 + i) * n + e + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int i = 0; i < CNT; ++i) v[u] = fma(-h[i], vv[u][i], v[u]);
+            w[e + u * stride] = v[u];
+            if (NORM) acc = fma(v[u], v[u], acc);
         }
     }
-    if (norm) {
-        const double s = block_sum(acc, sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = s;
-        last_block_reduce(partial, 1, 0, 1, out, ticket, sh);
+    for (; e < n; e += stride) {
+        double v = w[e];
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) v = fma(-h[i], V[(size_t)(i0 + i) * n + e], v);
+        w[e] = v;
+        if (NORM) acc = fma(v, v, acc);
+    }
+    if (NORM) {
+        double a1[1] = {acc};
+        block_partials<1>(a1, partial + blockIdx.x, sh);
+        last_block_reduce(partial, 1, 0, 1, out, ticket);
+    }
+}
+
+template <int CNT>
+void update_launch(double *w, const double *V, long long n, const double *hcoef, int i0, bool norm,
+                   double *partial, double *out, unsigned int *ticket, cudaStream_t st) {
+    if (norm) k_update<CNT, true><<<kRedBlocks, kRedThreads, 0, st>>>(w, V, n, hcoef, i0, partial, out, ticket);
+    else k_update<CNT, false><<<kRedBlocks, kRedThreads, 0, st>>>(w, V, n, hcoef, i0, partial, out, ticket);
+}
+
+// cnt in 1..kDotChunk
+void update_dispatch(int cnt, double *w, const double *V, long long n, const double *hcoef, int i0, bool norm,
+                     double *partial, double *out, unsigned int *ticket, cudaStream_t st) {
+    switch (cnt) {
+        case 1: update_launch<1>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 2: update_launch<2>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 3: update_launch<3>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 4: update_launch<4>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 5: update_launch<5>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 6: update_launch<6>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 7: update_launch<7>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 8: update_launch<8>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 9: update_launch<9>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 10: update_launch<10>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 11: update_launch<11>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 12: update_launch<12>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 13: update_launch<13>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 14: update_launch<14>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        case 15: update_launch<15>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
+        default: update_launch<16>(w, V, n, hcoef, i0, norm, partial, out, ticket, st); break;
     }
 }
 
@@ -156,9 +231,9 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const double *v, long lon
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
         acc = fma(v[e], v[e], acc);
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-    last_block_reduce(partial, 1, 0, 1, out, ticket, sh);
+    double a1[1] = {acc};
+    block_partials<1>(a1, partial + blockIdx.x, sh);
+    last_block_reduce(partial, 1, 0, 1, out, ticket);
 }
 
 __global__ void k_sub(double *r, const double *b, const double *y, long long n) {
@@ -232,8 +307,11 @@ struct Red {
     }
     sts_status update(double *w, const double *V, int k, const double *hcoef, int norm, double *out) {
         Krylov &K = h->kry;
-        k_update<<<kRedBlocks, kRedThreads, 0, h->stream>>>(w, V, n, hcoef, k, K.partial, norm, out, K.ticket);
-        STS_LAUNCHED();
+        for (int i0 = 0; i0 < k; i0 += kDotChunk) {
+            const int cnt = std::min(kDotChunk, k - i0);
+            update_dispatch(cnt, w, V, n, hcoef, i0, norm && i0 + cnt == k, K.partial, out, K.ticket, h->stream);
+            STS_LAUNCHED();
+        }
         return STS_OK;
     }
     sts_status norm2(const double *v, double *out) {
