@@ -89,9 +89,20 @@ typedef struct sts_jac_s *sts_jac_t;
  *                          diagonal blocks; rows sorted, every diagonal entry present.
  *   o_indptr[b+1], o_indices[nnz_o]   HOST int32.  CSR pattern of S_ij (i != j), shared
  *                          by all off-diagonal blocks (may be empty).
- *   r_diag, r_off          rank-one pairs per diagonal / off-diagonal block (>= 0).
- *                          The BR1-BSR pair_indptr of Section 5.1 follows from them:
- *                          pairs are numbered in block order.
+ *   r_diag, r_off          rank-one pairs per diagonal / off-diagonal block (>= 0),
+ *                          used when pair_indptr is NULL.  The BR1-BSR pair_indptr of
+ *                          Section 5.1 then follows from them: pairs are numbered in
+ *                          block order.
+ *   pair_indptr[nnzb+1]    HOST int32 or NULL.  The BR1-BSR pair_indptr of Section 5.1
+ *                          for pair counts that differ from block to block (Section 4.3:
+ *                          a diagonal block gathers one pair per source term and two per
+ *                          face, so boundary cells hold fewer): the pairs of block k are
+ *                          [pair_indptr[k], pair_indptr[k+1]).  pair_indptr[0] = 0 and it
+ *                          never decreases, else STS_ERR_INVALID_ARG.  When given,
+ *                          r_diag and r_off are ignored.  The handle stores every block
+ *                          with the largest count of its kind (diagonal / off-diagonal),
+ *                          the missing pairs as exact zeros, so memory and time follow
+ *                          those maxima.
  *   S, U, V                FP64 values.  S: block order, nnz_d values per diagonal
  *                          block and nnz_o per off-diagonal block, each in pattern
  *                          order.  U (column_data) and V (row_data): [n_pairs][b].
@@ -116,6 +127,7 @@ typedef struct {
     const int *o_indices;
     int r_diag;
     int r_off;
+    const int *pair_indptr;
     const double *S;
     const double *U;
     const double *V;

@@ -40,7 +40,7 @@ class sts_jac_desc(ctypes.Structure):
                 ("block_indptr", ctypes.c_void_p), ("block_indices", ctypes.c_void_p),
                 ("d_indptr", ctypes.c_void_p), ("d_indices", ctypes.c_void_p),
                 ("o_indptr", ctypes.c_void_p), ("o_indices", ctypes.c_void_p),
-                ("r_diag", ctypes.c_int), ("r_off", ctypes.c_int),
+                ("r_diag", ctypes.c_int), ("r_off", ctypes.c_int), ("pair_indptr", ctypes.c_void_p),
                 ("S", ctypes.c_void_p), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
                 ("values_on_host", ctypes.c_int), ("enable_transpose", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
@@ -147,8 +147,9 @@ class StsJacobian:
 
     ``w`` is any object exposing the public layout arrays (``block_indptr``,
     ``block_indices``, ``d_indptr``, ``d_indices``, ``o_indptr``, ``o_indices``,
-    ``r_diag``, ``r_off``, ``b``); ``S``, ``U``, ``V`` are FP64 torch CUDA tensors
-    or numpy arrays (host), in the public layout.
+    ``r_diag``, ``r_off``, ``b``, and optionally ``pair_indptr`` for per-block pair
+    counts); ``S``, ``U``, ``V`` are FP64 torch CUDA tensors or numpy arrays
+    (host), in the public layout.
     """
 
     def __init__(self, w, S, U, V, *, mixed: bool = False, layout: str = "cell",
@@ -161,6 +162,8 @@ class StsJacobian:
         self._idx = [np.ascontiguousarray(a, dtype=np.int32) for a in
                      (w.block_indptr, w.block_indices, w.d_indptr, w.d_indices, w.o_indptr,
                       w.o_indices)]
+        pip = getattr(w, "pair_indptr", None)
+        self._pip = None if pip is None else np.ascontiguousarray(pip, dtype=np.int32)
         self.stream = torch.cuda.current_stream() if stream is None else stream
         on_host = isinstance(S, np.ndarray)
         if on_host:
@@ -180,6 +183,7 @@ class StsJacobian:
          d.o_indices) = [a.ctypes.data for a in self._idx]
         d.r_diag = int(w.r_diag)
         d.r_off = int(w.r_off)
+        d.pair_indptr = None if self._pip is None else self._pip.ctypes.data
         d.S, d.U, d.V = _ptr(S), _ptr(U), _ptr(V)
         d.values_on_host = 1 if on_host else 0
         d.enable_transpose = 1 if transpose else 0
@@ -195,7 +199,8 @@ class StsJacobian:
         n_diag = int(np.sum(rows == bidx))
         n_off = int(bidx.shape[0]) - n_diag
         self.nnz_S = n_diag * int(self._idx[2][-1]) + n_off * int(self._idx[4][-1])
-        self.n_pairs = n_diag * int(w.r_diag) + n_off * int(w.r_off)
+        self.n_pairs = (int(self._pip[-1]) if self._pip is not None
+                        else n_diag * int(w.r_diag) + n_off * int(w.r_off))
 
     # -- lifetime
     def close(self):

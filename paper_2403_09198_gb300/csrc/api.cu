@@ -386,7 +386,7 @@ sts_status build_grad_tables(sts_jac_s *h) {
                     if (P.h_pslot_slot[q] == s) ++local;
                 for (int lane = 0; lane < kTile; ++lane) {
                     const int k = hblk[((size_t)t * P.n_slots + s) * kTile + lane];
-                    if (k < 0) continue;
+                    if (k < 0 || local >= h->pbase[k + 1] - h->pbase[k]) continue;   // padding pair
                     dst[h->pbase[k] + local] = (int)(((size_t)t * P.n_dtasks + ps) * kTile + lane);
                 }
             }
@@ -463,7 +463,24 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
     STS_TRY(check_csr(d->d_indptr, d->d_indices, b, b, true, "diagonal-block pattern"));
     STS_TRY(check_csr(d->o_indptr, d->o_indices, b, b, false, "off-diagonal-block pattern"));
     const int nnzb = d->block_indptr[nc];
-    const long long n_pairs = (long long)nc * d->r_diag + (long long)(nnzb - nc) * d->r_off;
+    // Pairs per block: uniform per block kind, or the caller's pair_indptr.  The
+    // handle stores every block with the largest count of its kind.
+    int r_diag = d->r_diag, r_off = d->r_off;
+    long long n_pairs = (long long)nc * r_diag + (long long)(nnzb - nc) * r_off;
+    if (d->pair_indptr) {
+        const int *pp = d->pair_indptr;
+        if (pp[0] != 0) return set_error(STS_ERR_INVALID_ARG, "sts_jac_create: pair_indptr[0] must be 0");
+        r_diag = r_off = 0;
+        for (int i = 0; i < nc; ++i)
+            for (int k = d->block_indptr[i]; k < d->block_indptr[i + 1]; ++k) {
+                const int cnt = pp[k + 1] - pp[k];
+                if (cnt < 0)
+                    return set_error(STS_ERR_INVALID_ARG, "sts_jac_create: pair_indptr decreases at block %d", k);
+                int &rmax = d->block_indices[k] == i ? r_diag : r_off;
+                rmax = std::max(rmax, cnt);
+            }
+        n_pairs = pp[nnzb];
+    }
     if (n_pairs > (1LL << 31) - 1) return set_error(STS_ERR_INVALID_ARG, "sts_jac_create: too many pairs");
     if (!d->S) return set_error(STS_ERR_INVALID_ARG, "sts_jac_create: S is NULL");
     if (n_pairs > 0 && (!d->U || !d->V)) return set_error(STS_ERR_INVALID_ARG, "sts_jac_create: U or V is NULL");
@@ -475,8 +492,8 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
     h->dtype = d->dtype;
     h->layout = d->vec_layout;
     h->rep = d->representation;
-    h->r_diag = d->r_diag;
-    h->r_off = d->r_off;
+    h->r_diag = r_diag;
+    h->r_off = r_off;
     h->nnz_d = d->d_indptr[b];
     h->nnz_o = d->o_indptr[b];
     h->nnzb = nnzb;
@@ -505,7 +522,8 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
         for (int k = h->bptr[i]; k < h->bptr[i + 1]; ++k) {
             const bool diag = h->bidx[k] == i;
             h->soff[k + 1] = h->soff[k] + (diag ? h->nnz_d : h->nnz_o);
-            h->pbase[k + 1] = h->pbase[k] + (diag ? h->r_diag : h->r_off);
+            h->pbase[k + 1] = d->pair_indptr ? d->pair_indptr[k + 1]
+                                             : h->pbase[k] + (diag ? h->r_diag : h->r_off);
         }
     h->nnz_S = h->soff[nnzb];
     sts_status st = STS_OK;

@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
 // Repack the public values into one stream of one direction.  Each stream
 // position (per tile and lane) is an S entry of a block slot, an entry of a
 // pair vector (the axpy vectors in the main stream, the dot vectors in the
-// pass-1 stream), or a zero.  With vec > 1 each run of vec positions of a
+// pass-1 stream), or a zero.  A block with fewer pairs than its kind's
+// largest count gets zero vectors in the remaining pair slots.  With vec > 1 each run of vec positions of a
 // lane is contiguous ([tile][position / vec][lane][vec]), for 16-byte loads.
 template <typename T>
 __global__ void k_repack(T *out, const double *S, const double *AX, const int *blk,
@@ -409,7 +410,8 @@ __global__ void k_repack(T *out, const double *S, const double *AX, const int *b
         } else {
             const int ps = -1 - kind;
             const int k = blk[((size_t)t * n_slots + pslot_slot[ps]) * kTile + lane];
-            if (k >= 0) v = AX[(size_t)(pbase[k] + pslot_local[ps]) * b + arg];
+            const int l = pslot_local[ps];
+            if (k >= 0 && l < pbase[k + 1] - pbase[k]) v = AX[(size_t)(pbase[k] + l) * b + arg];
         }
         out[i] = (T)v;
     }

@@ -656,7 +656,9 @@ __global__ void k_smw_spack(T *out, const double *lu, const double *dinv, const 
     }
 }
 
-// Repack diagonal-block values into [entry][cell] and the diagonal pairs into [k][q][cell].
+// Repack diagonal-block values into [entry][cell] and the diagonal pairs into
+// [k][q][cell]; a cell with fewer than r pairs gets zero pairs (u = v = 0 leaves
+// A_k unchanged and adds an identity row and column to C_k).
 __global__ void k_smw_repack(double *Sd, double *Ud, double *Vd, const double *S, const double *U,
                              const double *V, const int *diag_blk, const long long *soff,
                              const int *pbase, int nc, int ncp, int nnz_d, int b, int r) {
@@ -673,7 +675,7 @@ __global__ void k_smw_repack(double *Sd, double *Ud, double *Vd, const double *S
             const long long kq = j / ncp;
             const int q = (int)(kq % b), k = (int)(kq / b);
             double u = 0.0, v = 0.0;
-            if (cell < nc) {
+            if (cell < nc && k < pbase[diag_blk[cell] + 1] - pbase[diag_blk[cell]]) {
                 const size_t src = (size_t)(pbase[diag_blk[cell]] + k) * b + q;
                 u = U[src];
                 v = V[src];

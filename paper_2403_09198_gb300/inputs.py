@@ -24,6 +24,13 @@ Layout of one workload (all arrays numpy, C-contiguous):
   others nnz_o.  Pairs: ``r_diag`` per diagonal block and ``r_off`` per
   off-diagonal block, pair order = block order (BR1-BSR ``pair_indptr`` of
   Section 5.1); ``U`` (column_data) and ``V`` (row_data) are ``[n_pairs][b]``.
+* Per-block pair counts (Section 5.1 allows them to differ): ``pairs_per_face``
+  adds that many pairs to a diagonal block per face neighbour (Section 4.3: one
+  pair from the source term plus two per face flux, nine in the interior of a 2D
+  grid, fewer on its boundary); ``random_pair_max > 0`` instead draws every
+  block's count uniformly from ``0..random_pair_max`` with a generator of its
+  own (seed + 7919), so the value draws keep their order.  ``r_diag`` and
+  ``r_off`` of the returned workload are then the largest counts of each kind.
 
 Value distributions: diagonal entries of diagonal blocks ``1/dt + |z|``; every
 other S entry ``0.1 z``; ``u, v = z / sqrt(b)``; right-hand side ``z``; loss
@@ -189,9 +196,25 @@ def _standard_normal(rng: np.random.Generator, n: int, chunk: int = 1 << 24) -> 
     return out
 
 
+def pair_counts_for(block_indptr, block_indices, r_diag: int, r_off: int,
+                    pairs_per_face: int = 0, random_pair_max: int = 0, seed: int = 0) -> np.ndarray:
+    """int64 [nnzb]: pairs of every block (see the module docstring)."""
+    block_indptr = np.asarray(block_indptr, dtype=np.int64)
+    block_indices = np.asarray(block_indices, dtype=np.int64)
+    nc = block_indptr.shape[0] - 1
+    deg = np.diff(block_indptr) - 1
+    rows = np.repeat(np.arange(nc), np.diff(block_indptr))
+    is_diag = rows == block_indices
+    if random_pair_max > 0:
+        rng = np.random.default_rng(seed + 7919)
+        return rng.integers(0, random_pair_max + 1, size=block_indices.shape[0]).astype(np.int64)
+    return np.where(is_diag, r_diag + pairs_per_face * deg[rows], r_off).astype(np.int64)
+
+
 def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
                   r_diag: int = 2, r_off: int = 1, seed: int = 0, dt: float = 1e-3,
-                  same_pattern: bool = False, random_density: float = 0.0) -> Workload:
+                  same_pattern: bool = False, random_density: float = 0.0,
+                  pairs_per_face: int = 0, random_pair_max: int = 0) -> Workload:
     """Draw one workload; see the module docstring for shapes and distributions.
     ``random_density > 0`` replaces both patterns by random ones of that density."""
     Ly = Lx if Ly is None else Ly
@@ -210,7 +233,16 @@ def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
     is_diag = rows == block_indices
     n_off = int(nnzb - nc)
 
-    pair_indptr = pair_indptr_for(block_indptr, block_indices, r_diag, r_off)
+    if pairs_per_face or random_pair_max:
+        counts = pair_counts_for(block_indptr, block_indices, r_diag, r_off,
+                                 pairs_per_face, random_pair_max, seed)
+        pair_indptr = np.zeros(nnzb + 1, dtype=np.int64)
+        np.cumsum(counts, out=pair_indptr[1:])
+        pair_indptr = pair_indptr.astype(np.int32)
+        r_diag = int(counts[is_diag].max(initial=0))
+        r_off = int(counts[~is_diag].max(initial=0))
+    else:
+        pair_indptr = pair_indptr_for(block_indptr, block_indices, r_diag, r_off)
     n_pairs = int(pair_indptr[-1])
 
     nnz_d, nnz_o = d_indices.shape[0], o_indices.shape[0]
@@ -267,6 +299,9 @@ WORKLOADS = {
     "grid512_N60": dict(Lx=512, N=60, w=2, r_diag=2, r_off=1, seed=3),
     # 128x128 cells, N=60, adjoint gradients, seed 4
     "grid128_N60_adjoint": dict(Lx=128, N=60, w=2, r_diag=2, r_off=1, seed=4),
+    # 128x128 cells, N=60, the paper's physical pair counts: 1 + 2 per face on
+    # diagonal blocks (9 inside, 7 on edges, 5 in corners), 2 per neighbour block
+    "grid128_N60_pairs9": dict(Lx=128, N=60, w=2, r_diag=1, r_off=2, pairs_per_face=2, seed=5),
 }
 
 

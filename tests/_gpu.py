@@ -12,9 +12,9 @@ TOL64 = 1e-12
 # Small workloads the oracle finishes in seconds; together they cover several
 # tiles and ragged tails, one cell, 1 x L strips, N = 1, no pairs, the paper's
 # physical pair counts (9 per diagonal block, 2 per neighbour block), the
-# band +-4 / 3-pair family of the N = 200 workload, and two patterns outside the
+# band +-4 / 3-pair family of the N = 200 workload, two patterns outside the
 # paper's family (a shared pattern, random patterns) that take the generic
-# table-driven kernels.
+# table-driven kernels, and pair counts that differ from block to block.
 SMALL = {
     "grid16_N10": dict(Lx=16, N=10, w=2, r_diag=2, r_off=1, seed=0),
     "ragged5x3": dict(Lx=5, Ly=3, N=4, w=1, r_diag=2, r_off=1, seed=1),
@@ -26,6 +26,10 @@ SMALL = {
     "same_pattern": dict(Lx=8, Ly=4, N=6, w=2, r_diag=2, r_off=1, seed=7, same_pattern=True),
     "band4_r3": dict(Lx=33, Ly=2, N=12, w=4, r_diag=3, r_off=1, seed=8),
     "random_pattern": dict(Lx=7, Ly=6, N=9, r_diag=2, r_off=1, seed=10, random_density=0.3),
+    # per-block pair counts: 1 + 2 per face on diagonal blocks (9 / 7 / 5), 2 per
+    # neighbour block; and counts drawn from 0..3 per block, zero-pair blocks included
+    "pairs_faces": dict(Lx=6, Ly=5, N=8, w=2, r_diag=1, r_off=2, pairs_per_face=2, seed=11),
+    "pairs_random": dict(Lx=9, Ly=5, N=7, w=2, r_diag=0, r_off=0, random_pair_max=3, seed=12),
 }
 
 
@@ -33,7 +37,7 @@ def workload(name):
     return inputs.make_workload(**SMALL[name])
 
 
-@functools.lru_cache(maxsize=3)
+@functools.lru_cache(maxsize=4)
 def full(name):
     """A full-size named workload, generated once per test session."""
     return inputs.named_workload(name)

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts_match_header(lib):
     # int fields then pointers: a mismatch would shift the pointers
-    assert ctypes.sizeof(binding.sts_jac_desc) == 6 * 4 + 6 * 8 + 2 * 4 + 3 * 8 + 2 * 4 + 8
+    assert ctypes.sizeof(binding.sts_jac_desc) == 6 * 4 + 6 * 8 + 2 * 4 + 8 + 3 * 8 + 2 * 4 + 8
     assert ctypes.sizeof(binding.sts_gmres_info) == 4 * 4 + 8
 
 

@@ -85,16 +85,17 @@ def _sample_rows(w, rng, n_rand=3000):
     return np.unique(np.array(rows, dtype=np.int64))
 
 
-@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60"])
+@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60", "grid128_N60_pairs9"])
 def test_matvec_full_size_sampled(name):
     w = full(name)
     J = oracle_jac(w)
-    jac = _jac(w, transpose=(name == "grid128_N60"), layout="component")
+    both = name.startswith("grid128")
+    jac = _jac(w, transpose=both, layout="component")
     rng = np.random.default_rng(11)
     x = rng.standard_normal(w.n)
     rows = _sample_rows(w, rng)
     xi = to_component_major(x, w.n_cells, w.b)
-    for trans in ((False, True) if name == "grid128_N60" else (False,)):
+    for trans in ((False, True) if both else (False,)):
         y = from_component_major(host(jac.matvec(dev(xi), trans=trans)), w.n_cells, w.b)
         ref = oracle.matvec_rows(J, x, rows, trans=trans)
         assert rel_err(y[rows], ref) <= TOL64, trans
@@ -127,7 +128,7 @@ def _sample_cells(w, rng):
     return np.unique(np.concatenate([ends, rng.choice(nc, 300, replace=False)]))
 
 
-@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60"])
+@pytest.mark.parametrize("name", ["grid128_N60", "grid256_N200", "grid512_N60", "grid128_N60_pairs9"])
 def test_bjacobi_full_size_sampled(name):
     """Full-size workloads on sampled cells.  On 256 x 256 and 512 x 512 cells
     each apply warp streams several tiles in a row (its ring runs on across
@@ -175,7 +176,7 @@ def test_bjacobi_errors():
 # ---------------------------------------------------------------- GMRES
 
 
-@pytest.mark.parametrize("case", ["grid16_N10", "weak_diag_restart", "long_cycle"])
+@pytest.mark.parametrize("case", ["grid16_N10", "weak_diag_restart", "long_cycle", "pairs_random"])
 def test_gmres_parity(case):
     """GMRES against the oracle's textbook GMRES.  long_cycle runs 25 Arnoldi
     steps in one cycle (no preconditioner, restart 40), so the multi-dot
@@ -185,6 +186,8 @@ def test_gmres_parity(case):
         w, m = workload("grid16_N10"), 20
     elif case == "weak_diag_restart":
         w, m = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 4
+    elif case == "pairs_random":
+        w, m = inputs.make_workload(6, 5, N=4, w=2, random_pair_max=4, seed=9, dt=0.5), 4
     else:
         w, m, pc = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 40, "none"
     J = oracle_jac(w)
@@ -345,7 +348,7 @@ def test_mixed_precision_fgmres(dt):
 
 
 def test_grad_matches_oracle_outer_products():
-    for name in ("ragged5x3", "pairs9_2", "band4_r3"):
+    for name in ("ragged5x3", "pairs9_2", "band4_r3", "pairs_faces", "pairs_random"):
         w = workload(name)
         J = oracle_jac(w)
         jac = _jac(w, transpose=True)
@@ -423,7 +426,7 @@ def test_adjoint_full_size_sampled():
 # ---------------------------------------------------------------- dense-BSR baseline
 
 
-@pytest.mark.parametrize("name", ["grid16_N10", "ragged5x3", "pairs9_2", "band4_r3"])
+@pytest.mark.parametrize("name", ["grid16_N10", "ragged5x3", "pairs9_2", "band4_r3", "pairs_random"])
 def test_dense_bsr_baseline(name):
     w = workload(name)
     J = oracle_jac(w)

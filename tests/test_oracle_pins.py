@@ -149,10 +149,14 @@ def test_matvec_r0_is_csr_spmv():
     np.testing.assert_allclose(oracle.matvec(J, x, trans=True), A.T @ x, rtol=1e-14, atol=1e-12)
 
 
-@pytest.mark.parametrize("same_pattern", [False, True])
-def test_matvec_factored_route(same_pattern):
-    """Dense assembly equals the factored route S x + sum_p u_p (v_p . x_j)."""
-    wl = _tiny(Lx=4, Ly=3, N=4, w=2, same_pattern=same_pattern)
+@pytest.mark.parametrize("kw", [{}, dict(same_pattern=True),
+                                dict(r_diag=1, r_off=2, pairs_per_face=2),
+                                dict(random_pair_max=3)],
+                         ids=["uniform", "same_pattern", "pairs_per_face", "random_counts"])
+def test_matvec_factored_route(kw):
+    """Dense assembly equals the factored route S x + sum_p u_p (v_p . x_j),
+    also with pair counts that differ from block to block (Section 5.1)."""
+    wl = _tiny(Lx=4, Ly=3, N=4, w=2, **kw)
     J = oracle.Jacobian.from_workload(wl)
     A = _global_csr(wl)
     x = np.random.default_rng(2).standard_normal(wl.n)
@@ -169,6 +173,39 @@ def test_matvec_factored_route(same_pattern):
     assert is_diag.sum() == wl.n_cells
     np.testing.assert_allclose(oracle.matvec(J, x), y, rtol=1e-13, atol=1e-12)
     np.testing.assert_allclose(oracle.matvec(J, x, trans=True), yt, rtol=1e-13, atol=1e-12)
+
+
+def _pad_pairs(wl, r_diag, r_off):
+    """The same Jacobian with every block padded to r_diag / r_off pairs by zero pairs."""
+    counts = np.diff(wl.pair_indptr)
+    target = np.where(wl.is_diag_block(), r_diag, r_off)
+    assert np.all(target >= counts)
+    pip = np.zeros(wl.nnzb + 1, dtype=np.int64)
+    np.cumsum(target, out=pip[1:])
+    U = np.zeros((pip[-1], wl.b))
+    V = np.zeros((pip[-1], wl.b))
+    for k in range(wl.nnzb):
+        c = counts[k]
+        U[pip[k]:pip[k] + c] = wl.U[wl.pair_indptr[k]:wl.pair_indptr[k + 1]]
+        V[pip[k]:pip[k] + c] = wl.V[wl.pair_indptr[k]:wl.pair_indptr[k + 1]]
+    return oracle.Jacobian(n_cells=wl.n_cells, b=wl.b, block_indptr=wl.block_indptr,
+                           block_indices=wl.block_indices, d_indptr=wl.d_indptr,
+                           d_indices=wl.d_indices, o_indptr=wl.o_indptr, o_indices=wl.o_indices,
+                           pair_indptr=pip.astype(np.int32), S=wl.S, U=U, V=V)
+
+
+def test_non_uniform_pairs_equal_zero_padding():
+    """Per-block pair counts: padding every block with zero pairs to a uniform
+    count leaves the operator and its block-Jacobi inverse unchanged (u v^T = 0)."""
+    wl = _tiny(Lx=4, Ly=3, N=4, w=2, seed=13, random_pair_max=3)
+    assert len(set(np.diff(wl.pair_indptr).tolist())) > 1 and np.min(np.diff(wl.pair_indptr)) == 0
+    J = oracle.Jacobian.from_workload(wl)
+    Jp = _pad_pairs(wl, wl.r_diag + 1, wl.r_off + 2)
+    x = np.random.default_rng(3).standard_normal(wl.n)
+    for trans in (False, True):
+        np.testing.assert_array_equal(oracle.matvec(Jp, x, trans=trans), oracle.matvec(J, x, trans=trans))
+        np.testing.assert_array_equal(oracle.bj_apply(oracle.bj_setup(Jp), x, trans=trans),
+                                      oracle.bj_apply(oracle.bj_setup(J), x, trans=trans))
 
 
 def test_matvec_adjoint_identity():
