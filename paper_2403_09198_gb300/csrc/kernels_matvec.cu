@@ -196,19 +196,27 @@ __global__ void __launch_bounds__(128) k_mv_main(MvArgs<T> a) {
 //                the pair terms u_k[p] c_k.
 //   flow row N+f: sum over slots of the pass-1 flow dots, then the pair terms.
 // Held in registers for the whole group: the flow-column x values of every
-// slot, the pass-1 pair dots c_k (when there are at most kStructRegPairs), and
-// a sliding window of the 2 WD + 1 own-cell x values of the band; the x values
-// of the next row are loaded one row ahead.  Each row's coefficients (s_rl
-// positions, contiguous) are staged in shared memory by one bulk copy, two
-// rows per warp in flight.
-constexpr int kStructRegPairs = 8;
+// slot, the pass-1 pair dots c_k (NREG = 8: up to 8 of them; NREG = 32: up to
+// 32; NREG = 0: read per row), and a sliding window of the 2 WD + 1 own-cell x
+// values of the band; the x values of the next row are loaded one row ahead.
+// Each row's coefficients (s_rl positions, contiguous) are staged in shared
+// memory by one bulk copy, two rows per warp in flight.
+//
+// Pair terms in registers run as fall-through switches (Duff's device), so
+// register indices stay static and no FP64 FMA is issued for a missing term (a
+// predicated-off FMA still takes its pipe slot).  NREG = 8: term k sits in
+// cq[8 - nps + k] and the switch enters at case 8 - nps.  NREG = 32: with more
+// than 16 terms the first 16 sit in cq[0..16) and run as one block; the other
+// m <= 16 terms sit at the end of cq[16..32) and the switch enters at 16 - m.
+constexpr int kStructDuff = 16;
 
 __host__ __device__ inline size_t mv_struct_warp_bytes(int rl, int elem) {
     return 128 + 2 * (size_t)rl * kTile * elem;     // two mbarriers (padded), two row stages
 }
 
-template <typename T, int WD, bool CREG>
+template <typename T, int WD, int NREG>
 __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
+    static_assert(NREG == 0 || NREG == 8 || NREG == 2 * kStructDuff, "register pair slots");
     constexpr int NF = kStructNF;
     constexpr int NS = kStructMaxSlots;
     constexpr int BANDW = 2 * WD + 1;
@@ -291,13 +299,17 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) xf[s][f] = s < ns ? __ldg(xs[s] + (size_t)(N + f) * ncp) : T(0);
     }
-    // pair dots in registers, aligned to the end: term k sits in slot poff + k, so
-    // a jump to case poff runs exactly the nps terms in order (no idle FMA slots)
-    const int poff = CREG ? kStructRegPairs - nps : 0;
-    T cq[CREG ? kStructRegPairs : 1];
+    // pair dots in registers (see above): an optional block of RB = 16, then the
+    // last m terms aligned to the end of the D switch slots
+    constexpr int D = NREG == 8 ? 8 : kStructDuff, RB = NREG > D ? D : 0;
+    const bool blk = RB > 0 && nps > D;
+    const int m = blk ? nps - D : nps, poff = D - m;
+    T cq[NREG > 0 ? NREG : 1];
 #pragma unroll
-    for (int i = 0; i < (CREG ? kStructRegPairs : 0); ++i)
-        cq[i] = i >= poff ? __ldg(cc + (size_t)(i - poff) * kTile) : T(0);
+    for (int i = 0; i < RB; ++i) cq[i] = blk ? __ldg(cc + (size_t)i * kTile) : T(0);
+#pragma unroll
+    for (int i = 0; i < (NREG > 0 ? D : 0); ++i)
+        cq[RB + i] = i >= poff ? __ldg(cc + (size_t)((blk ? D : 0) + i - poff) * kTile) : T(0);
     // band window: xb[k] = x_own[p - WD + k] (clipped; clipped entries carry zero coefficients)
     T xb[BANDW];
 #pragma unroll
@@ -348,8 +360,7 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
             }
         }
         const T *vu = v + (BANDW + NF + (ns - 1) * (1 + NF)) * kTile;
-        if (CREG) {
-            static_assert(kStructRegPairs == 8, "one case per slot");
+        if constexpr (NREG == 8) {
             const T *vo = vu - poff * kTile;
             switch (poff) {
                 case 0: acc = fma(vo[0 * kTile], cq[0], acc); [[fallthrough]];
@@ -360,6 +371,33 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
                 case 5: acc = fma(vo[5 * kTile], cq[5], acc); [[fallthrough]];
                 case 6: acc = fma(vo[6 * kTile], cq[6], acc); [[fallthrough]];
                 case 7: acc = fma(vo[7 * kTile], cq[7], acc); [[fallthrough]];
+                default: break;
+            }
+        } else if constexpr (NREG > 0) {
+            static_assert(kStructDuff == 16, "one case per slot");
+            if (blk) {
+#pragma unroll
+                for (int i = 0; i < RB; ++i) acc = fma(vu[i * kTile], cq[i], acc);
+            }
+            const T *vo = vu + ((blk ? D : 0) - poff) * kTile;
+            const T *c = cq + RB;
+            switch (poff) {
+                case 0: acc = fma(vo[0 * kTile], c[0], acc); [[fallthrough]];
+                case 1: acc = fma(vo[1 * kTile], c[1], acc); [[fallthrough]];
+                case 2: acc = fma(vo[2 * kTile], c[2], acc); [[fallthrough]];
+                case 3: acc = fma(vo[3 * kTile], c[3], acc); [[fallthrough]];
+                case 4: acc = fma(vo[4 * kTile], c[4], acc); [[fallthrough]];
+                case 5: acc = fma(vo[5 * kTile], c[5], acc); [[fallthrough]];
+                case 6: acc = fma(vo[6 * kTile], c[6], acc); [[fallthrough]];
+                case 7: acc = fma(vo[7 * kTile], c[7], acc); [[fallthrough]];
+                case 8: acc = fma(vo[8 * kTile], c[8], acc); [[fallthrough]];
+                case 9: acc = fma(vo[9 * kTile], c[9], acc); [[fallthrough]];
+                case 10: acc = fma(vo[10 * kTile], c[10], acc); [[fallthrough]];
+                case 11: acc = fma(vo[11 * kTile], c[11], acc); [[fallthrough]];
+                case 12: acc = fma(vo[12 * kTile], c[12], acc); [[fallthrough]];
+                case 13: acc = fma(vo[13 * kTile], c[13], acc); [[fallthrough]];
+                case 14: acc = fma(vo[14 * kTile], c[14], acc); [[fallthrough]];
+                case 15: acc = fma(vo[15 * kTile], c[15], acc); [[fallthrough]];
                 default: break;
             }
         } else {
@@ -524,6 +562,11 @@ sts_status dots_launch(sts_jac_s *h, const MvArgs<T> &a) {
     return STS_OK;
 }
 
+template <typename T, int WD>
+void (*mv_struct_kernel(int nreg))(MvArgs<T>) {
+    return nreg == 8 ? k_mv_struct<T, WD, 8> : nreg ? k_mv_struct<T, WD, 2 * kStructDuff> : k_mv_struct<T, WD, 0>;
+}
+
 template <typename T>
 sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
     STS_TRY(dots_launch<T>(h, a));
@@ -533,13 +576,13 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
         constexpr int kWarpsPerBlock = 2;      // two row stages per warp; small blocks pack the SM finely
         const size_t smem = (size_t)kWarpsPerBlock * mv_struct_warp_bytes(a.s_rl, (int)sizeof(T));
         void (*kern)(MvArgs<T>) = nullptr;
-        const bool creg = a.n_pslots <= kStructRegPairs;
+        const int nreg = a.n_pslots <= 8 ? 8 : a.n_pslots <= 2 * kStructDuff ? 2 * kStructDuff : 0;
         switch (a.wd) {
-            case 0: kern = creg ? k_mv_struct<T, 0, true> : k_mv_struct<T, 0, false>; break;
-            case 1: kern = creg ? k_mv_struct<T, 1, true> : k_mv_struct<T, 1, false>; break;
-            case 2: kern = creg ? k_mv_struct<T, 2, true> : k_mv_struct<T, 2, false>; break;
-            case 3: kern = creg ? k_mv_struct<T, 3, true> : k_mv_struct<T, 3, false>; break;
-            default: kern = creg ? k_mv_struct<T, 4, true> : k_mv_struct<T, 4, false>; break;
+            case 0: kern = mv_struct_kernel<T, 0>(nreg); break;
+            case 1: kern = mv_struct_kernel<T, 1>(nreg); break;
+            case 2: kern = mv_struct_kernel<T, 2>(nreg); break;
+            case 3: kern = mv_struct_kernel<T, 3>(nreg); break;
+            default: kern = mv_struct_kernel<T, 4>(nreg); break;
         }
         int &resident = h->mvs_blocks[sizeof(T) == 8 ? 0 : 1];    // blocks resident at once, found once
         if (!resident) {

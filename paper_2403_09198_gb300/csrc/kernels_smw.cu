@@ -289,11 +289,19 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
 //                          coefficients of the flow rows in column i, which
 //                          feed NF independent accumulators;
 //   forward flow rows:    the 3 coefficients among the flow unknowns;
-//   backward flow rows:   pivot inverse and coefficients, then the r dot-vector
-//                          entries of t = V^T x0 for that unknown;
+//   backward flow rows:   per row its pivot inverse and coefficients, then the
+//                          RMAX dot-vector entries of t = V^T x0 for that unknown
+//                          (one group, or one group per row where the three
+//                          rows are wider than a chunk);
 //   backward level row i: pivot inverse, NF flow coefficients, W band
-//                          coefficients (farthest first), r dot-vector entries;
-//   tail:                 W[a][q] for the correction x = x0 - W C^-1 t.
+//                          coefficients (farthest first), RMAX dot-vector entries;
+//   tail:                 W[a][q] for the correction x = x0 - W C^-1 t, with
+//                          C^-1 read per cell (FP64, r x r registers); in the
+//                          instances that fold (sap_fold) the capacitance solve
+//                          is folded into the tail instead: (W C^-1)[q][a],
+//                          formed in FP64 when the stream is packed, and
+//                          x = x0 - (W C^-1) t needs neither C^-1 nor its registers.
+// A cell with fewer than RMAX pairs has zero dot and tail entries.
 // The band recurrences keep their last W values in registers, so the only
 // dependency chain is one FMA per row.
 //
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
 template <typename T>
 struct SApplyArgs {
     const T *st;            // [n_tiles][Lt / VEC][32][VEC]
-    const double *Cinv;     // [r][r][ncp]
+    const double *Cinv;     // [r][r][ncp] (instances that do not fold only)
     const T *x;
     T *y;
     int *err;               // set when a bounded wait gave up
@@ -320,6 +328,23 @@ struct SApplyArgs {
 constexpr int kApWarps = 4;              // consumer warps per block of the structured apply (one per sub-partition)
 constexpr int kSApStages = 5;            // ring stages of the structured apply (three chunks in flight)
 constexpr int kSApChunkBytes = 8192;     // bytes per stage (one bulk copy)
+
+// Pair slots RMAX of the structured apply instance for r pairs per diagonal
+// block and band half-width w: 2, 4, or nine (one source pair plus two per face
+// of a 2D cell, Section 4.3).  Ten for w = 4, whose backward rows are then 18
+// positions wide instead of 17 (two 17-wide rows would not fit one chunk), and
+// for w = 2, whose 16-wide rows then form one-row groups: the extra zero slot
+// costs two FMAs per row but frees the registers a second row would hold.
+// 0: more pairs than any structured instance holds.
+__host__ __device__ constexpr int sap_rmax_big(int w) { return w == 2 || w == 4 ? 10 : 9; }
+__host__ __device__ constexpr int sap_rmax(int r, int w) {
+    return r <= 2 ? 2 : r <= 4 ? 4 : r <= sap_rmax_big(w) ? sap_rmax_big(w) : 0;
+}
+// Whether the instance folds C^-1 into its tail vectors: always above four
+// pairs, and wherever the r x r FP64 registers of the unfolded form would spill
+// (more than two pairs, or band half-width 1 or 4, by the ptxas register
+// reports).  Where both fit, the unfolded form measured faster (band 2, two pairs).
+__host__ __device__ constexpr bool sap_fold(int rmax, int w) { return rmax > 2 || w == 1 || w == 4; }
 
 __host__ __device__ constexpr int sap_gcd(int a, int b) { return b == 0 ? a : sap_gcd(b, a % b); }
 // rows per group for rows of `width` positions, VEC positions per vector
@@ -427,10 +452,14 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     constexpr int K = kSApChunkBytes / (kTile * (int)sizeof(T));
     constexpr int FW = W + NF, UF = sap_fwd_rows(FW, VEC, NF), GF = UF * FW;
     constexpr int GFF = sap_round(3, VEC), GBF = sap_round(6 + 3 * RMAX, VEC);
+    // the three backward flow rows form one group, or one group each where that is wider than a chunk
+    constexpr bool FSPLIT = GBF > K;
+    constexpr int G2 = sap_round(1 + RMAX, VEC), G1 = sap_round(2 + RMAX, VEC), G0 = sap_round(3 + RMAX, VEC);
     constexpr int BW = 1 + NF + W + RMAX, UB = sap_group_rows(BW, VEC), GB = UB * BW;
     constexpr int UT = sap_group_rows(RMAX, VEC), GT = UT * RMAX;
     static_assert(GF % VEC == 0 && GB % VEC == 0 && GT % VEC == 0, "groups are whole vectors");
-    static_assert(GF <= K && GBF <= K && GB <= K && GT <= K, "groups fit a chunk");
+    static_assert(GF <= K && G0 <= K && GB <= K && GT <= K, "groups fit a chunk");
+    constexpr bool FOLD = sap_fold(RMAX, W);
     static_assert(UF <= NF + 1, "forward rows read past N stay inside the block");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -502,14 +531,16 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     cp_async_commit();
     for (int k = 0; k < my; ++k) {
         const int cell = (gw + k * nw) * kTile + lane;
-        double cz[RMAX * RMAX];                 // C^-1 (transposed for A^T), zero outside r x r
+        double cz[FOLD ? 1 : RMAX * RMAX];      // C^-1 (transposed for A^T), zero outside r x r
+        if constexpr (!FOLD) {
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i)
+            for (int i = 0; i < RMAX; ++i)
 #pragma unroll
-            for (int l = 0; l < RMAX; ++l)
-                cz[i * RMAX + l] = (i < r && l < r)
-                                       ? __ldg(a.Cinv + (a.trans ? (size_t)l * r + i : (size_t)i * r + l) * P + cell)
-                                       : 0.0;
+                for (int l = 0; l < RMAX; ++l)
+                    cz[i * RMAX + l] =
+                        (i < r && l < r) ? __ldg(a.Cinv + (a.trans ? (size_t)l * r + i : (size_t)i * r + l) * P + cell)
+                                         : 0.0;
+        }
         cp_async_wait<0>();
         __syncwarp();
         // ---- forward sweep over the level rows: row i = [W band, oldest first | NF flow]
@@ -547,19 +578,32 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
         for (int q = 0; q < RMAX; ++q) t[q] = T(0);
         T xf[NF];
         {
-            // [d2, V(N+2) | d1, u(N+1,N+2), V(N+1) | d0, u(N,N+1), u(N,N+2), V(N)], V padded to RMAX
-            Group<T, GBF> g;
-            g.load(R.take(GBF));
-            xf[2] = g[0] * wf[2];
+            // rows [d2, V(N+2) | d1, u(N+1,N+2), V(N+1) | d0, u(N,N+1), u(N,N+2), V(N)], V padded to RMAX
+            auto flow = [&](auto e2, auto e1, auto e0) {
+                xf[2] = e2(0) * wf[2];
 #pragma unroll
-            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[1 + q], xf[2], t[q]);
-            constexpr int o1 = 1 + RMAX, o0 = o1 + 2 + RMAX;
-            xf[1] = fma(-g[o1 + 1], xf[2], g[o1] * wf[1]);
+                for (int q = 0; q < RMAX; ++q) t[q] = fma(e2(1 + q), xf[2], t[q]);
+                xf[1] = fma(-e1(1), xf[2], e1(0) * wf[1]);
 #pragma unroll
-            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[o1 + 2 + q], xf[1], t[q]);
-            xf[0] = fma(-g[o0 + 2], xf[2], fma(-g[o0 + 1], xf[1], g[o0] * wf[0]));
+                for (int q = 0; q < RMAX; ++q) t[q] = fma(e1(2 + q), xf[1], t[q]);
+                xf[0] = fma(-e0(2), xf[2], fma(-e0(1), xf[1], e0(0) * wf[0]));
 #pragma unroll
-            for (int q = 0; q < RMAX; ++q) t[q] = fma(g[o0 + 3 + q], xf[0], t[q]);
+                for (int q = 0; q < RMAX; ++q) t[q] = fma(e0(3 + q), xf[0], t[q]);
+            };
+            if constexpr (FSPLIT) {
+                Group<T, G2> g2;
+                Group<T, G1> g1;
+                Group<T, G0> g0;
+                g2.load(R.take(G2));
+                g1.load(R.take(G1));
+                g0.load(R.take(G0));
+                flow([&](int e) { return g2[e]; }, [&](int e) { return g1[e]; }, [&](int e) { return g0[e]; });
+            } else {
+                constexpr int o1 = 1 + RMAX, o0 = o1 + 2 + RMAX;
+                Group<T, GBF> g;
+                g.load(R.take(GBF));
+                flow([&](int e) { return g[e]; }, [&](int e) { return g[o1 + e]; }, [&](int e) { return g[o0 + e]; });
+            }
         }
         if (R.failed) goto fail;
         // ---- backward level rows i = N-1-j: [pivot inverse | NF flow | W band, farthest first | V (RMAX)]
@@ -586,15 +630,20 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) wl[(N + f) * kTile] = xf[f];
-        // ---- z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q])
+        // ---- z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q]);
+        //      folded: z = t and tail row q = (W C^-1)[q][0..RMAX)
         {
             T z[RMAX];
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
-                double sacc = 0.0;
+                if constexpr (FOLD) {
+                    z[i] = t[i];
+                } else {
+                    double sacc = 0.0;
 #pragma unroll
-                for (int l = 0; l < RMAX; ++l) sacc = fma(cz[i * RMAX + l], (double)t[l], sacc);
-                z[i] = (T)sacc;
+                    for (int l = 0; l < RMAX; ++l) sacc = fma(cz[i * RMAX + l], (double)t[l], sacc);
+                    z[i] = (T)sacc;
+                }
             }
             const bool more = k + 1 < my;
             const T *xn = a.x + (size_t)cell + (size_t)nw * kTile;
@@ -626,10 +675,14 @@ fail:
 //   src >= 0: LU slot (times the pivot inverse of row arg if arg >= 0)
 //   src = -1: pivot inverse of row arg      src = -2: dot vector entry arg
 //   src = -3: W entry arg                   src = -4: zero
+//   src = -5: folded tail entry arg = a * b + q: (W C^-1)[q][a] =
+//             sum_l W[l][q] C^-1[l][a], or for the transposed operator
+//             sum_l W'[l][q] C^-1[a][l] (C^-T), in FP64
 // Output element i is (tile, vector, lane, element) of the layout above.
 template <typename T>
 __global__ void k_smw_spack(T *out, const double *lu, const double *dinv, const double *DV, const double *WW,
-                            const int *src, const int *arg, int Lt, int ncp) {
+                            const double *Cinv, const int *src, const int *arg, int Lt, int ncp, int b, int r,
+                            int trans) {
     constexpr int VEC = 16 / (int)sizeof(T);
     const long long per_tile = (long long)Lt * kTile;
     const long long total = per_tile * (ncp / kTile);
@@ -651,6 +704,12 @@ __global__ void k_smw_spack(T *out, const double *lu, const double *dinv, const 
             v = DV[(size_t)ag * ncp + cell];
         } else if (sv == -3) {
             v = WW[(size_t)ag * ncp + cell];
+        } else if (sv == -5) {
+            const int aa = ag / b, q = ag - aa * b;
+            for (int l = 0; l < r; ++l) {
+                const double c = Cinv[(size_t)(trans ? aa * r + l : l * r + aa) * ncp + cell];
+                v = fma(WW[((size_t)l * b + q) * ncp + cell], c, v);
+            }
         }
         out[i] = (T)v;
     }
@@ -822,12 +881,12 @@ sts_status smw_build(sts_jac_s *h) {
     }
     // structured apply tables (both directions; FP64 and, for mixed handles, FP32)
     const int sw = struct_band(b, h->dptr, h->didx);
-    M.structured = sw >= 0 && h->r_diag <= 4 && M.nnz_lu == h->nnz_d;
+    M.structured = sw >= 0 && sap_rmax(h->r_diag, sw) > 0 && M.nnz_lu == h->nnz_d;
     if (M.structured) {
         const int NF = kStructNF, N = b - NF, r = h->r_diag;
         M.s_w = sw;
         auto sl = [&](int i, int j) { return slot[(size_t)i * b + j]; };
-        const int RMAX = r <= 2 ? 2 : 4;       // must match the kernel instance chosen at apply time
+        const int RMAX = sap_rmax(r, sw);      // the kernel instance chosen at apply time
         for (int prec = 0; prec < 2; ++prec) {
             if (prec == 1 && h->dtype != STS_MIXED) continue;
             const int elem = prec == 0 ? 8 : 4, vec = 16 / elem, K = kSApChunkBytes / (kTile * elem);
@@ -881,11 +940,14 @@ sts_status smw_build(sts_jac_s *h) {
                 lo(N + 2, N);
                 lo(N + 2, N + 1);
                 group();
+                const bool fsplit = sap_round(6 + 3 * RMAX, vec) > K;   // as FSPLIT in the kernel
                 put(-1, N + 2);
                 vd(N + 2);
+                if (fsplit) group();
                 put(-1, N + 1);
                 up(N + 1, N + 2);
                 vd(N + 1);
+                if (fsplit) group();
                 put(-1, N);
                 up(N, N + 1);
                 up(N, N + 2);
@@ -911,13 +973,14 @@ sts_status smw_build(sts_jac_s *h) {
                     group();
                 }
                 const int UT = sap_group_rows(RMAX, vec);
+                const int tail_src = sap_fold(RMAX, sw) ? -5 : -3;
                 for (int q0 = 0; q0 < b; q0 += UT) {
                     for (int q = q0; q < q0 + UT; ++q) {
                         if (q >= b) {
                             zero(RMAX);
                             continue;
                         }
-                        for (int k = 0; k < RMAX; ++k) put(k < r ? -3 : -4, k < r ? k * b + q : 0);
+                        for (int k = 0; k < RMAX; ++k) put(k < r ? tail_src : -4, k < r ? k * b + q : 0);
                     }
                     group();
                 }
@@ -927,7 +990,7 @@ sts_status smw_build(sts_jac_s *h) {
                 }
                 if (!fits) return set_error(STS_ERR_INVALID_ARG, "internal: structured apply group wider than a chunk");
                 for (size_t e = 0; e < src.size(); ++e)
-                    if (src[e] < -4 || (src[e] >= 0 && src[e] >= M.nnz_lu))
+                    if (src[e] < -5 || (src[e] >= 0 && src[e] >= M.nnz_lu))
                         return set_error(STS_ERR_INVALID_ARG, "internal: structured apply table");
                 M.s_lt[prec] = (int)src.size();
                 STS_TRY(upload(h, &M.spk_src[prec][dir], src));
@@ -1019,15 +1082,15 @@ sts_status smw_setup(sts_jac_s *h) {
         const double *WW = dir == 0 ? M.W : M.Wt;
         if (M.structured) {
             const long long n64 = (long long)M.s_lt[0] * P;
-            k_smw_spack<double><<<grid_for(n64, 256), 256, 0, h->stream>>>(M.ap64[dir], M.lu, M.dinv, DV, WW,
-                                                                            M.spk_src[0][dir], M.spk_arg[0][dir],
-                                                                            M.s_lt[0], h->ncp);
+            k_smw_spack<double><<<grid_for(n64, 256), 256, 0, h->stream>>>(
+                M.ap64[dir], M.lu, M.dinv, DV, WW, M.Cinv, M.spk_src[0][dir], M.spk_arg[0][dir], M.s_lt[0],
+                h->ncp, b, r, dir);
             STS_LAUNCHED();
             if (M.ap32[dir]) {
                 const long long n32 = (long long)M.s_lt[1] * P;
-                k_smw_spack<float><<<grid_for(n32, 256), 256, 0, h->stream>>>(M.ap32[dir], M.lu, M.dinv, DV, WW,
-                                                                              M.spk_src[1][dir], M.spk_arg[1][dir],
-                                                                              M.s_lt[1], h->ncp);
+                k_smw_spack<float><<<grid_for(n32, 256), 256, 0, h->stream>>>(
+                    M.ap32[dir], M.lu, M.dinv, DV, WW, M.Cinv, M.spk_src[1][dir], M.spk_arg[1][dir], M.s_lt[1],
+                    h->ncp, b, r, dir);
                 STS_LAUNCHED();
             }
             continue;
@@ -1071,6 +1134,12 @@ static sts_status smw_apply_t(sts_jac_s *h, int dir, const T *st, const T *dv, c
     return STS_OK;
 }
 
+template <typename T, int W>
+static void (*sap_kernel(int rmax))(SApplyArgs<T>) {
+    return rmax == 2 ? k_smw_sapply<T, W, 2> : rmax == 4 ? k_smw_sapply<T, W, 4>
+                                                          : k_smw_sapply<T, W, sap_rmax_big(W)>;
+}
+
 template <typename T>
 static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T *z) {
     const SmwPlan &M = h->smw;
@@ -1085,13 +1154,13 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
         return set_error(STS_ERR_INVALID_ARG, "block size %d needs %zu bytes of shared memory per warp", h->b, per_warp);
     const size_t smem = (size_t)wpb * per_warp;
     void (*kern)(SApplyArgs<T>) = nullptr;
-    const bool r2 = a.r <= 2;
+    const int rm = sap_rmax(h->r_diag, M.s_w);
     switch (M.s_w) {
-        case 0: kern = r2 ? k_smw_sapply<T, 0, 2> : k_smw_sapply<T, 0, 4>; break;
-        case 1: kern = r2 ? k_smw_sapply<T, 1, 2> : k_smw_sapply<T, 1, 4>; break;
-        case 2: kern = r2 ? k_smw_sapply<T, 2, 2> : k_smw_sapply<T, 2, 4>; break;
-        case 3: kern = r2 ? k_smw_sapply<T, 3, 2> : k_smw_sapply<T, 3, 4>; break;
-        default: kern = r2 ? k_smw_sapply<T, 4, 2> : k_smw_sapply<T, 4, 4>; break;
+        case 0: kern = sap_kernel<T, 0>(rm); break;
+        case 1: kern = sap_kernel<T, 1>(rm); break;
+        case 2: kern = sap_kernel<T, 2>(rm); break;
+        case 3: kern = sap_kernel<T, 3>(rm); break;
+        default: kern = sap_kernel<T, 4>(rm); break;
     }
     bool &attr = h->sap_attr[sizeof(T) == 8 ? 0 : 1];
     if (!attr && smem > 48 * 1024)
