@@ -452,6 +452,8 @@ def run_report(args):
     nsweep  matvec time and handle memory vs N, factored vs dense, fitted exponents;
     large   256x256, N=200: factored vs dense matvec, apply, setup, GMRES time to 1e-10;
     mixed   512x512, N=60: FP64 GMRES vs FP32/FP64 flexible GMRES, error vs the oracle;
+    pairs   128x128, N=60 with the paper's pair counts (1 + 2 per face, 2 per neighbour
+            block): factored vs dense matvec, apply, setup, GMRES, roofline fractions;
     kernels 128x128, N=60: three rounds of FP64 and FP32 matvec and apply, a short
             fixed launch sequence for kernel profilers (no timing)."""
     import numpy as np
@@ -542,6 +544,56 @@ def run_report(args):
         print(json.dumps(out), flush=True)
         return
 
+    if args.report == "pairs":
+        # the paper's pair counts (Section 4.3): 1 + 2 per face on diagonal blocks,
+        # 2 per neighbour block; algorithmic bytes count each block's own pairs
+        w = inputs.named_workload("grid128_N60_pairs9")
+        S, U, V, b = t(w.S), t(w.U), t(w.V), t(w.rhs)
+        x = torch.randn(w.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        counts = np.diff(w.pair_indptr)
+        rd = counts[w.is_diag_block()]
+        mv_bytes = 8 * (w.S.shape[0] + 2 * w.n_pairs * w.b + 2 * w.n) + 4 * w.nnzb
+        mv_flops = 2 * (w.S.shape[0] + 2 * w.n_pairs * w.b)
+        ap_bytes = 8 * (int(np.sum(w.nnz_d + 2 * rd * w.b + rd * rd)) + 2 * w.n)
+        hbm_peak, sm_mhz, src = _peaks()
+        fp64_peak = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        out = {"report": "pairs",
+               "workload": "grid128_N60_pairs9: 128x128 cells, N=60, b=63, band +-2, diagonal blocks "
+                           "1 + 2 pairs per face (9 inside, 7 on edges, 5 at corners), 2 per neighbour block",
+               "n_pairs": w.n_pairs, "diag_pair_counts": {str(k): int(np.sum(rd == k)) for k in np.unique(rd)},
+               "matvec_algorithmic_bytes": mv_bytes, "matvec_flops": mv_flops, "apply_algorithmic_bytes": ap_bytes}
+        for name, kw in (("factored", {}), ("dense", {"dense": True})):
+            j = StsJacobian(w, S, U, V, layout="component", **kw)
+            r = {"matvec_ms": avg(lambda: j.matvec(x, out=y), 10 if kw else 200),
+                 "memory_GB": j.memory_bytes() / 1e9}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            j.bjacobi_setup()
+            r["setup_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["apply_ms"] = avg(lambda: j.bjacobi_apply(x, out=y), 10 if kw else 200)
+            j.gmres(b, rtol=1e-10, restart=30)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = j.gmres(b, rtol=1e-10, restart=30)
+            r["gmres_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["gmres_iterations"] = info.iterations
+            r["gmres_true_rel_residual"] = info.true_rel_residual
+            out[name] = r
+            j.close()
+            torch.cuda.empty_cache()
+        f = out["factored"]
+        f["matvec_TFLOPs"] = mv_flops / (f["matvec_ms"] * 1e-3) / 1e12
+        f["matvec_frac_fp64_peak"] = f["matvec_TFLOPs"] / fp64_peak
+        f["matvec_GBps"] = mv_bytes / (f["matvec_ms"] * 1e-3) / 1e9
+        f["apply_GBps"] = ap_bytes / (f["apply_ms"] * 1e-3) / 1e9
+        f["matvec_frac_hbm"] = f["matvec_GBps"] / hbm_peak
+        f["apply_frac_hbm"] = f["apply_GBps"] / hbm_peak
+        out["peaks"] = {"hbm_GBps": hbm_peak, "fp64_TFLOPs": fp64_peak, "source": src}
+        out["speedup"] = {k: out["dense"][k] / f[k] for k in ("matvec_ms", "apply_ms", "setup_ms", "gmres_ms")}
+        print(json.dumps(out), flush=True)
+        return
+
     if args.report == "mixed":
         import oracle
         oracle.build()
@@ -607,7 +659,7 @@ def main():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels"], default=None,
+    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels", "pairs"], default=None,
                    help="print an extra measurement instead of the benchmark line")
     args = p.parse_args()
     if args.report:
