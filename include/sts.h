@@ -148,6 +148,8 @@ typedef struct {
     double inner_rtol;    /* mixed mode: relative reduction per cycle (default 1e-6)          */
     int vectors_on_host;  /* 1: b and x are host pointers (copied in and out inside the call) */
     double *history;      /* optional host array [max_iters]: rotated residual / ||b|| per step */
+    int left;             /* 1: left preconditioning, (M A) x = M b (Section 6, Eq.
+                             left_precond_system); needs STS_PRECOND_BJ, not mixed       */
 } sts_gmres_opts;
 
 /* Result of sts_gmres_solve. */
@@ -245,6 +247,11 @@ sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int 
  * (Section 6, Eq. right_precond_system; Saad & Schultz), classical Gram-Schmidt
  * with a second pass, Givens rotations on the host in FP64.  x holds the
  * initial guess on entry and the solution on exit (pass zeros for x0 = 0).
+ * Left preconditioning (opts.left, Eq. left_precond_system): each cycle starts
+ * from z = M (b - J x), the Arnoldi operator is M J, x += V y, and a cycle stops
+ * once |g| has fallen below ||z|| times the factor rtol ||b|| / ||b - J x|| that
+ * the true residual still needs; history then holds |g| / ||z|| times the
+ * cycle's starting true relative residual.
  * Mixed mode: FP32 matvec and block-Jacobi, FP64 Krylov basis, Arnoldi,
  * residual refresh and capacitance solves, flexible GMRES.  Convergence is
  * declared on the FP64 true residual only.  Synchronous; info may be NULL.
@@ -290,6 +297,121 @@ sts_status sts_selftest_bounded_wait(void *stream);
 
 /* Destroy a handle and free its device memory.  NULL is accepted. */
 sts_status sts_jac_destroy(sts_jac_t h);
+
+/* ---------------------------------------------------------------------------
+ * Jacobian generator of a toy flow model: the first-order finite-volume
+ * residual with an HLL flux (Section 3.2, Eq. HLL_flux; Section 3.3, Eq.
+ * system_residual) and its Jacobian dR/dQ written directly in the BR1-BSR form
+ * above, the flux Jacobians split as in Section 4.1 (Eqs. r1_flux_left /
+ * r1_flux_right) into a sparse part plus two rank-one pairs per face.
+ *
+ * Model, per cell q = (rho_0 .. rho_{N-1}, u, v, T), block size b = N + 3
+ * (Section 2.1 with synthetic constants):
+ *   e_k(T) = e0_k + cv_k T,  p = sum rho_k r_k T,  rho e_tot = sum rho_k e_k + rho (u^2+v^2)/2,
+ *   gamma = (c_v + r) / c_v with c_v, r the mass-fraction averages of cv_k, r_k,
+ *   a = sqrt(gamma r T);  conserved u(q) = (rho_k, rho u, rho v, rho e_tot);
+ *   f_n(q) = (rho_k u_n, rho u u_n + p n_x, rho v u_n + p n_y, (rho e_tot + p) u_n).
+ *   HLL wave-speed bounds: s_L = min(0, u_nL - a_L, u_nR - a_R),
+ *   s_R = max(0, u_nL + a_L, u_nR + a_R), ties to the first candidate.
+ *   Source (level rows only): Omega_k = -sum_{|l-k|<=w} K[k][l-k+w] rho_l
+ *                                       + ws_k A exp(-theta/T) sum_l beta_l rho_l.
+ * Grid: Lx x Ly unit cells, id iy*Lx + ix, faces to i-Lx, i-1, i+1, i+Lx with
+ * outward unit normals; no flux through the outer boundary.
+ *   R_i = u(q_i) - u(q_i^n) + dt (sum over faces f(q_i, q_j, n_ij) - Omega(q_i)).
+ * Jacobian layout (sts_flow_get_layout):
+ *   block CSR: the mesh adjacency including the diagonal, rows ascending;
+ *   diagonal pattern: level row p holds columns max(0,p-w)..min(N-1,p+w) then
+ *     N, N+1, N+2; the three flow rows are dense;
+ *   neighbour pattern: level row p holds p, N, N+1, N+2; flow rows dense;
+ *   pairs of the diagonal block of cell i (1 + 2 per face): (-dt ws, d omega/dq),
+ *     then per face in block order (-dt (f_R - f_L), d a_f / d q_i) and
+ *     (dt (u_R - u_L), d c_f / d q_i), with a_f = (s_L + s_R) / (2 (s_R - s_L)),
+ *     c_f = s_L s_R / (s_R - s_L), L = i and R = the neighbour;
+ *   pairs of the neighbour block (i, j): the same two face vectors with
+ *     d a_f / d q_j and d c_f / d q_j;
+ *   S values: diagonal block H(q_i) + dt (sum over faces A0_L + K band), with
+ *     H = du/dq and A0_L = (1/2 + a_f) A_n(q_i) - c_f H(q_i); neighbour block
+ *     dt A0_R = dt ((1/2 - a_f) A_n(q_j) + c_f H(q_j)).
+ * States must have sum rho_k > 0, sum rho_k cv_k > 0, sum rho_k r_k > 0 and
+ * T > 0; others give NaN or infinite values (not checked on the device).
+ */
+typedef struct {
+    int Lx, Ly;                 /* grid size (>= 1 each)                                  */
+    int n_species;              /* N >= 1                                                  */
+    int band;                   /* w >= 0: level band of K and of the diagonal pattern     */
+    const double *r;            /* HOST [N] species gas constants (> 0)                    */
+    const double *cv;           /* HOST [N] specific heats (> 0)                           */
+    const double *e0;           /* HOST [N] energies at T = 0                              */
+    const double *beta;         /* HOST [N] source weights                                 */
+    const double *ws;           /* HOST [N] source stoichiometry                           */
+    const double *K;            /* HOST [N][2w+1] band, K[k][l - k + w]                    */
+    double A, theta;            /* source rate A exp(-theta / T)                           */
+    double dt;                  /* pseudo time step                                        */
+    void *stream;               /* cudaStream_t for all work (NULL = legacy default)       */
+} sts_flow_desc;
+
+typedef struct {
+    int n_cells, block_size, nnzb, nnz_d, nnz_o, n_pairs;
+    long long nnz_S;            /* length of S                                             */
+} sts_flow_sizes;
+
+typedef struct sts_flow_s *sts_flow_t;
+
+/* Copy the constants and build the layout tables.  STS_ERR_INVALID_ARG on a bad size, a
+ * NULL array, r_k <= 0 or cv_k <= 0, or a non-finite constant. */
+sts_status sts_flow_create(const sts_flow_desc *d, sts_flow_t *out);   /* b = N + 3 <= 256 */
+/* Sizes of the layout and of the S, U, V arrays (U, V: [n_pairs][block_size]). */
+sts_status sts_flow_get_sizes(sts_flow_t f, sts_flow_sizes *s);
+/* Copy the layout into HOST int32 arrays sized by sts_flow_get_sizes (block_indptr
+ * n_cells+1, block_indices nnzb, d_indptr / o_indptr b+1, d_indices nnz_d, o_indices
+ * nnz_o, pair_indptr nnzb+1); they can be handed to sts_jac_create as they are. */
+sts_status sts_flow_get_layout(sts_flow_t f, int *block_indptr, int *block_indices, int *d_indptr,
+                               int *d_indices, int *o_indptr, int *o_indices, int *pair_indptr);
+/* R = residual of the states Q given Qn; DEVICE pointers, [n_cells][b] cell-major; async. */
+sts_status sts_flow_residual(sts_flow_t f, const double *Q, const double *Qn, double *R);
+/* S, U, V of dR/dQ at Q in the layout above; DEVICE pointers; async. */
+sts_status sts_flow_jacobian(sts_flow_t f, const double *Q, double *S, double *U, double *V);
+/* Free the generator.  NULL is accepted. */
+sts_status sts_flow_destroy(sts_flow_t f);
+
+/*
+ * One implicit pseudo-time step by Newton's method (Section 3.3): starting from
+ * the Q given, iterate Q <- Q + alpha dQ with (dR/dQ) dQ = -R(Q) (Eq.
+ * LinearSystem), the Jacobian written by sts_flow_jacobian into jac
+ * (sts_jac_update_values), block-Jacobi set up and the system solved by
+ * sts_gmres_solve with opts->gmres.  alpha (the line-search coefficient) starts
+ * at 1 and is halved while ||R|| does not decrease, at most max_halvings times.
+ * A linear solve that stops at max_iters without converging still gives a step
+ * (inexact Newton).  Stops when ||R(Q)||_2 <= max(rtol ||R(Q^0)||, atol).
+ *   jac: a factored handle created from this generator's layout
+ *        (sts_flow_get_layout), vec_layout STS_LAYOUT_CELL_MAJOR; its values are
+ *        overwritten.
+ *   Q: DEVICE [n_cells][b], the initial iterate on entry, the result on exit;
+ *   Qn: DEVICE, the previous time level.
+ * Synchronous.  STS_ERR_NOT_CONVERGED (Q holds the last accepted iterate) when
+ * max_newton iterations end above the tolerance or the line search finds no
+ * decrease; the errors of the calls it makes pass through.
+ */
+typedef struct {
+    int max_newton;           /* Newton iterations (default 20)                          */
+    double rtol;              /* relative tolerance on ||R|| (default 1e-10)             */
+    double atol;              /* absolute tolerance on ||R|| (default 0)                 */
+    int max_halvings;         /* line-search halvings of alpha (default 8)               */
+    sts_gmres_opts gmres;     /* linear solves; vectors_on_host must be 0                */
+    double *history;          /* optional HOST [max_newton + 1]: ||R|| before iteration 1,
+                                 then after every iteration                              */
+} sts_newton_opts;
+
+typedef struct {
+    int iterations;           /* Newton iterations taken                                 */
+    int linear_iterations;    /* GMRES iterations over all solves                        */
+    int halvings;             /* line-search halvings over all iterations                */
+    int converged;
+    double res0, res;         /* ||R(Q^0)||_2 and ||R(Q)||_2 at exit                     */
+} sts_newton_info;
+
+sts_status sts_flow_newton(sts_flow_t f, sts_jac_t jac, double *Q, const double *Qn,
+                           const sts_newton_opts *opts, sts_newton_info *info);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,13 @@ x += M (V_k y_k) with R y_k = g.  At every restart and at the end the true
 residual ||b - A x|| / ||b|| is recomputed and convergence is declared only on
 it.  A happy breakdown is taken when h_{j+1,j} <= 1e-14 ||w||, ||w|| the norm of
 A M v_j before orthogonalisation.
+
+Left preconditioning (Section 6, Eq. left_precond_system, (M A) x = M b): a cycle
+starts from z = M (b - A x), the Arnoldi operator is M A, the correction is
+x += V_k y_k, and a cycle stops when |g_{j+1}| has fallen below ||z|| times the
+factor rtol ||b|| / ||b - A x|| that the true residual still needs; the
+history holds |g_{j+1}| / ||z|| times the cycle's starting true relative
+residual.  Convergence is again declared only on the recomputed true residual.
 """
 from __future__ import annotations
 
@@ -21,7 +28,7 @@ from .native import Jacobian, bj_apply, bj_setup, matvec
 
 
 def _gmres_core(A: Callable, M: Callable, b: np.ndarray, m: int, rtol: float,
-                max_iters: int, x0=None):
+                max_iters: int, x0=None, left: bool = False):
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     bnorm = float(np.linalg.norm(b))
@@ -46,11 +53,21 @@ def _gmres_core(A: Callable, M: Callable, b: np.ndarray, m: int, rtol: float,
         cs = np.zeros(m)
         sn = np.zeros(m)
         g = np.zeros(m + 1)
-        g[0] = beta
-        Vb[0] = r / beta
+        if left:
+            z = M(r)
+            g0 = float(np.linalg.norm(z))
+            Vb[0] = z / g0
+            stop = g0 * (rtol * bnorm / beta)
+            scale = beta / (g0 * bnorm)
+        else:
+            g0 = beta
+            Vb[0] = r / beta
+            stop = rtol * bnorm
+            scale = 1.0 / bnorm
+        g[0] = g0
         k = 0
         for j in range(m):
-            w = A(M(Vb[j]))
+            w = M(A(Vb[j])) if left else A(M(Vb[j]))
             w0 = float(np.linalg.norm(w))
             for i in range(j + 1):                  # modified Gram-Schmidt
                 H[i, j] = float(np.dot(w, Vb[i]))
@@ -69,25 +86,25 @@ def _gmres_core(A: Callable, M: Callable, b: np.ndarray, m: int, rtol: float,
             g[j] = cs[j] * g[j]
             its += 1
             k = j + 1
-            info["history"].append(abs(g[j + 1]) / bnorm)
+            info["history"].append(abs(g[j + 1]) * scale)
             happy = hj1 <= 1e-14 * w0
             if happy:
                 info["breakdown"] = True
-            if happy or abs(g[j + 1]) / bnorm <= rtol or its >= max_iters:
+            if happy or abs(g[j + 1]) <= stop or its >= max_iters:
                 break
             Vb[j + 1] = w / hj1
         y = np.zeros(k)
         for i in range(k - 1, -1, -1):              # back substitution R y = g
             y[i] = (g[i] - np.dot(H[i, i + 1:k], y[i + 1:k])) / H[i, i]
-        x = x + M(Vb[:k].T @ y)
+        x = x + (Vb[:k].T @ y if left else M(Vb[:k].T @ y))
         info["restarts"] += 1
     info["iterations"] = its
     return x, info
 
 
 def gmres(J: Jacobian, b, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1000,
-          precond: str = "bj", trans: bool = False, x0=None, factors=None):
-    """Solve J x = b (or J^T x = b) with block-Jacobi right preconditioning.
+          precond: str = "bj", trans: bool = False, x0=None, factors=None, left: bool = False):
+    """Solve J x = b (or J^T x = b) with block-Jacobi right (``left``: left) preconditioning.
 
     Returns ``(x, info)``; ``info`` holds iterations, restarts, the per-iteration
     rotated residual history, the final true relative residual and ``converged``.
@@ -107,11 +124,11 @@ def gmres(J: Jacobian, b, restart: int = 30, rtol: float = 1e-10, max_iters: int
     def A(v):
         return matvec(J, v, trans=trans)
 
-    return _gmres_core(A, M, b, restart, rtol, max_iters, x0=x0)
+    return _gmres_core(A, M, b, restart, rtol, max_iters, x0=x0, left=left)
 
 
 def gmres_operator(A: Callable, M: Callable, b, restart: int, rtol: float,
-                   max_iters: int = 1000, x0=None):
+                   max_iters: int = 1000, x0=None, left: bool = False):
     """The same textbook GMRES on caller-supplied operators (small dense tests)."""
     b = np.ascontiguousarray(b, dtype=np.float64).ravel()
-    return _gmres_core(A, M, b, restart, rtol, max_iters, x0=x0)
+    return _gmres_core(A, M, b, restart, rtol, max_iters, x0=x0, left=left)

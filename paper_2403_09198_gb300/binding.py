@@ -30,7 +30,8 @@ ABI_FUNCTIONS = ["sts_last_error", "sts_version", "sts_jac_create", "sts_jac_upd
                  "sts_jac_matvec", "sts_jac_matvec_noalloc", "sts_jac_matvec_f32", "sts_jac_bjacobi_setup",
                  "sts_jac_bjacobi_apply", "sts_jac_bjacobi_apply_f32", "sts_gmres_solve",
                  "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_selftest_bounded_wait",
-                 "sts_jac_destroy"]
+                 "sts_jac_destroy", "sts_flow_create", "sts_flow_get_sizes", "sts_flow_get_layout",
+                 "sts_flow_residual", "sts_flow_jacobian", "sts_flow_newton", "sts_flow_destroy"]
 
 
 class sts_jac_desc(ctypes.Structure):
@@ -46,11 +47,35 @@ class sts_jac_desc(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class sts_flow_desc(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("n_species", ctypes.c_int), ("band", ctypes.c_int),
+                ("r", ctypes.c_void_p), ("cv", ctypes.c_void_p), ("e0", ctypes.c_void_p),
+                ("beta", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("K", ctypes.c_void_p),
+                ("A", ctypes.c_double), ("theta", ctypes.c_double), ("dt", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class sts_flow_sizes(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int), ("block_size", ctypes.c_int), ("nnzb", ctypes.c_int),
+                ("nnz_d", ctypes.c_int), ("nnz_o", ctypes.c_int), ("n_pairs", ctypes.c_int),
+                ("nnz_S", ctypes.c_longlong)]
+
+
 class sts_gmres_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("flexible", ctypes.c_int), ("trans", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("vectors_on_host", ctypes.c_int), ("history", ctypes.c_void_p)]
+                ("vectors_on_host", ctypes.c_int), ("history", ctypes.c_void_p), ("left", ctypes.c_int)]
+
+
+class sts_newton_opts(ctypes.Structure):
+    _fields_ = [("max_newton", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("gmres", sts_gmres_opts), ("history", ctypes.c_void_p)]
+
+
+class sts_newton_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("linear_iterations", ctypes.c_int), ("halvings", ctypes.c_int),
+                ("converged", ctypes.c_int), ("res0", ctypes.c_double), ("res", ctypes.c_double)]
 
 
 class sts_gmres_info(ctypes.Structure):
@@ -98,6 +123,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                 "sts_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
                 "sts_selftest_bounded_wait": [P],
                 "sts_jac_destroy": [P],
+                "sts_flow_create": [ctypes.POINTER(sts_flow_desc), ctypes.POINTER(P)],
+                "sts_flow_get_sizes": [P, ctypes.POINTER(sts_flow_sizes)],
+                "sts_flow_get_layout": [P, P, P, P, P, P, P, P],
+                "sts_flow_residual": [P, P, P, P],
+                "sts_flow_jacobian": [P, P, P, P, P],
+                "sts_flow_newton": [P, P, P, P, ctypes.POINTER(sts_newton_opts), ctypes.POINTER(sts_newton_info)],
+                "sts_flow_destroy": [P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -246,7 +278,8 @@ class StsJacobian:
 
     def gmres(self, b, x0=None, *, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1000,
               precond: str = "bj", trans: bool = False, mixed: bool = False,
-              inner_rtol: float = 0.0, history: bool = False, raise_on_fail: bool = True):
+              inner_rtol: float = 0.0, history: bool = False, raise_on_fail: bool = True,
+              left: bool = False):
         """Solve J x = b (J^T x = b).  ``b``: CUDA tensor or numpy array (host)."""
         import torch
         on_host = isinstance(b, np.ndarray)
@@ -258,7 +291,7 @@ class StsJacobian:
         o = sts_gmres_opts()
         o.restart, o.max_iters, o.rtol = restart, max_iters, rtol
         o.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
-        o.trans, o.mixed, o.inner_rtol = int(trans), int(mixed), inner_rtol
+        o.trans, o.mixed, o.inner_rtol, o.left = int(trans), int(mixed), inner_rtol, int(left)
         o.vectors_on_host = int(on_host)
         hist = np.zeros(max_iters) if history else None
         o.history = hist.ctypes.data if history else None
@@ -283,3 +316,122 @@ class StsJacobian:
         n = ctypes.c_size_t()
         check(self.lib.sts_jac_memory(self.h, ctypes.byref(n)))
         return int(n.value)
+
+
+@dataclass
+class FlowLayout:
+    """BR1-BSR layout of the flow Jacobian, accepted by ``StsJacobian`` as it is."""
+    N: int
+    b: int
+    r_diag: int
+    r_off: int
+    block_indptr: np.ndarray
+    block_indices: np.ndarray
+    d_indptr: np.ndarray
+    d_indices: np.ndarray
+    o_indptr: np.ndarray
+    o_indices: np.ndarray
+    pair_indptr: np.ndarray
+    nnz_S: int
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.pair_indptr[-1])
+
+
+class StsFlow:
+    """Owner of one ``sts_flow_t``: residual and r1-sparse Jacobian of the toy
+    HLL-flux model for the constants and grid of ``case`` (an
+    ``inputs.FlowCase``, or any object with the same fields)."""
+
+    def __init__(self, case, stream=None):
+        import torch
+        self.lib = load()
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._c = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                   (case.r, case.cv, case.e0, case.beta, case.ws, case.K)]
+        d = sts_flow_desc()
+        d.Lx, d.Ly, d.n_species, d.band = int(case.Lx), int(case.Ly), int(case.N), int(case.w)
+        d.r, d.cv, d.e0, d.beta, d.ws, d.K = [a.ctypes.data for a in self._c]
+        d.A, d.theta, d.dt = float(case.A), float(case.theta), float(case.dt)
+        d.stream = self.stream.cuda_stream
+        h = ctypes.c_void_p()
+        check(self.lib.sts_flow_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        z = sts_flow_sizes()
+        check(self.lib.sts_flow_get_sizes(self.h, ctypes.byref(z)))
+        self.sizes = z
+        nc, b = z.n_cells, z.block_size
+        arrs = [np.zeros(n, dtype=np.int32) for n in (nc + 1, z.nnzb, b + 1, z.nnz_d, b + 1, z.nnz_o, z.nnzb + 1)]
+        check(self.lib.sts_flow_get_layout(self.h, *[a.ctypes.data for a in arrs]))
+        counts = np.diff(arrs[6])
+        rows = np.repeat(np.arange(nc), np.diff(arrs[0]))
+        diag = rows == arrs[1]
+        self.layout = FlowLayout(N=int(case.N), b=b, r_diag=int(counts[diag].max(initial=0)),
+                                 r_off=int(counts[~diag].max(initial=0)), block_indptr=arrs[0],
+                                 block_indices=arrs[1], d_indptr=arrs[2], d_indices=arrs[3],
+                                 o_indptr=arrs[4], o_indices=arrs[5], pair_indptr=arrs[6],
+                                 nnz_S=int(z.nnz_S))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sts_flow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def residual(self, Q, Qn, out=None):
+        """R(Q) given the previous level Qn; CUDA float64 tensors [n_cells, b]."""
+        import torch
+        R = torch.empty_like(Q) if out is None else out
+        check(self.lib.sts_flow_residual(self.h, _ptr(Q), _ptr(Qn), _ptr(R)))
+        return R
+
+    def jacobian(self, Q, S=None, U=None, V=None):
+        """(S, U, V) of dR/dQ at Q in ``self.layout``; CUDA float64 tensors."""
+        import torch
+        z, dev = self.sizes, Q.device
+        S = torch.empty(z.nnz_S, dtype=torch.float64, device=dev) if S is None else S
+        U = torch.empty((z.n_pairs, z.block_size), dtype=torch.float64, device=dev) if U is None else U
+        V = torch.empty_like(U) if V is None else V
+        check(self.lib.sts_flow_jacobian(self.h, _ptr(Q), _ptr(S), _ptr(U), _ptr(V)))
+        return S, U, V
+
+    def jacobian_handle(self, **kw):
+        """A factored, cell-major ``StsJacobian`` of this layout (values of the
+        flow Jacobian at the states ``kw.pop('Q')`` if given, else zeros with
+        unit S diagonal-free placeholders), for ``newton``."""
+        import torch
+        Q = kw.pop("Q", None)
+        if Q is None:
+            z = self.sizes
+            S = torch.zeros(z.nnz_S, dtype=torch.float64, device="cuda")
+            U = torch.zeros((z.n_pairs, z.block_size), dtype=torch.float64, device="cuda")
+            V = torch.zeros_like(U)
+        else:
+            S, U, V = self.jacobian(Q)
+        return StsJacobian(self.layout, S, U, V, layout="cell", n_levels=self.layout.N, **kw)
+
+    def newton(self, jac, Q, Qn, *, max_newton: int = 20, rtol: float = 1e-10, atol: float = 0.0,
+               max_halvings: int = 8, gmres_rtol: float = 1e-10, restart: int = 30, gmres_max_iters: int = 1000,
+               precond: str = "bj", left: bool = False, raise_on_fail: bool = True):
+        """One pseudo-time step by Newton's method; Q (CUDA [n_cells, b]) is updated
+        in place.  Returns (info dict, history of ||R||)."""
+        o = sts_newton_opts()
+        o.max_newton, o.rtol, o.atol, o.max_halvings = max_newton, rtol, atol, max_halvings
+        o.gmres.restart, o.gmres.max_iters, o.gmres.rtol = restart, gmres_max_iters, gmres_rtol
+        o.gmres.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
+        o.gmres.left = int(left)
+        hist = np.zeros(max_newton + 1)
+        o.history = hist.ctypes.data
+        info = sts_newton_info()
+        st = self.lib.sts_flow_newton(self.h, jac.h, _ptr(Q), _ptr(Qn), ctypes.byref(o), ctypes.byref(info))
+        if raise_on_fail:
+            check(st)
+        d = dict(iterations=info.iterations, linear_iterations=info.linear_iterations, halvings=info.halvings,
+                 converged=bool(info.converged), res0=info.res0, res=info.res, status=st)
+        return d, hist[:info.iterations + 1].copy()

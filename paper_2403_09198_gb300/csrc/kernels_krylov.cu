@@ -9,6 +9,10 @@
 // this equals x += M (V y)).  Convergence is declared on the recomputed true
 // residual only.  Mixed mode (flexible GMRES): z_j = M32(v_j) and w = A32 z_j in
 // FP32; the basis, the orthogonalisation, x and the residual refresh stay FP64.
+// Left preconditioning (Eq. left_precond_system, (M A) x = M b): the cycle's
+// first vector is M r / ||M r||, each step forms w = M (A v_j), x += V y, and a
+// cycle stops when the preconditioned residual has fallen by the factor the
+// true residual still needs.
 //
 // All reductions are deterministic: a fixed grid writes per-block partial sums
 // and the block that finishes last adds them in a fixed order.
@@ -374,6 +378,9 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
     const bool pre = d.precond != STS_PRECOND_NONE;
     const int dir = d.trans ? 1 : 0;
     const bool mixed = d.mixed != 0;
+    const bool left = d.left != 0;
+    if (left && (!pre || mixed))
+        return set_error(STS_ERR_INVALID_ARG, "gmres: left preconditioning needs precond BJ and mixed = 0");
     if (d.precond != STS_PRECOND_BJ && d.precond != STS_PRECOND_NONE)
         return set_error(STS_ERR_INVALID_ARG, "gmres: unknown precond %d", d.precond);
     if (m > 512) return set_error(STS_ERR_INVALID_ARG, "gmres: restart %d exceeds 512", m);
@@ -433,17 +440,35 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
             inf.true_rel_residual = beta / bnorm;
             if (beta / bnorm <= rtol) { inf.converged = 1; break; }
             if (its >= max_iters) { inf.converged = 0; break; }
-            const double stop_abs = mixed ? std::max(rtol * bnorm, inner * beta) : rtol * bnorm;
-            k_scale<<<nb, 256, 0, h->stream>>>(K.V, K.r, 1.0 / beta, n);
+            double stop_abs = mixed ? std::max(rtol * bnorm, inner * beta) : rtol * bnorm;
+            double g0 = beta, hscale = 1.0 / bnorm;
+            if (left) {
+                // z = M r; the cycle works on the preconditioned residual
+                STS_TRY(opM64(h, dir, K.r, K.tmp));
+                STS_TRY(R.norm2(K.tmp, K.red));
+                STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaStreamSynchronize(h->stream));
+                g0 = std::sqrt(hp[0]);
+                if (!std::isfinite(g0) || g0 == 0.0) {
+                    status = set_error(STS_ERR_NUMERIC, "gmres: preconditioned residual norm is %g", g0);
+                    break;
+                }
+                stop_abs = g0 * (rtol * bnorm / beta);
+                hscale = beta / (g0 * bnorm);
+            }
+            k_scale<<<nb, 256, 0, h->stream>>>(K.V, left ? K.tmp : K.r, 1.0 / g0, n);
             STS_LAUNCHED();
             std::fill(g.begin(), g.end(), 0.0);
-            g[0] = beta;
+            g[0] = g0;
             int k = 0;
             for (int j = 0; j < m; ++j) {
                 NvtxRange nvtx_step("gmres arnoldi step");
                 double *vj = K.V + (size_t)j * n;
-                // z_j = M v_j, w = A z_j
-                if (!mixed) {
+                // z_j = M v_j, w = A z_j (left: w = M (A v_j))
+                if (left) {
+                    STS_TRY(opA64(h, dir, vj, K.tmp));
+                    STS_TRY(opM64(h, dir, K.tmp, K.w));
+                } else if (!mixed) {
                     double *zj = K.Z + (size_t)j * n;
                     if (pre) STS_TRY(opM64(h, dir, vj, zj));
                     else STS_CK(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -490,7 +515,7 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
                 g[j] = cs[j] * g[j];
                 ++its;
                 k = j + 1;
-                if (d.history && its <= max_iters) d.history[its - 1] = std::fabs(g[j + 1]) / bnorm;
+                if (d.history && its <= max_iters) d.history[its - 1] = std::fabs(g[j + 1]) * hscale;
                 const bool happy = hn <= 1e-14 * w0;
                 if (happy || std::fabs(g[j + 1]) <= stop_abs || its >= max_iters) break;
                 k_scale<<<nb, 256, 0, h->stream>>>(K.V + (size_t)(j + 1) * n, K.w, 1.0 / hn, n);
@@ -504,7 +529,7 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
             }
             std::copy(y.begin(), y.begin() + k, hp);
             STS_CK(cudaMemcpyAsync(K.red, hp, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-            if (!mixed) k_axpy_multi<double><<<nb, 256, 0, h->stream>>>(K.xb, K.Z, n, K.red, k);
+            if (!mixed) k_axpy_multi<double><<<nb, 256, 0, h->stream>>>(K.xb, left ? K.V : K.Z, n, K.red, k);
             else k_axpy_multi<float><<<nb, 256, 0, h->stream>>>(K.xb, K.Z32, n, K.red, k);
             STS_LAUNCHED();
             ++inf.restarts;

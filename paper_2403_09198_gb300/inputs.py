@@ -287,6 +287,68 @@ def make_workload(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2,
                     rhs=rhs, W=W, seed=seed)
 
 
+@dataclasses.dataclass
+class FlowCase:
+    """Inputs of the toy flow model whose HLL-flux Jacobian is built in r1-sparse form:
+    per-species constants, source constants, pseudo time step, and two state fields
+    (current iterate Q and previous time level Qn, [nc][b] with b = N + 3, variables
+    rho_0..rho_{N-1}, u, v, T).  Nondimensional synthetic values (no rate data)."""
+
+    Lx: int
+    Ly: int
+    N: int
+    w: int
+    r: np.ndarray           # [N] species gas constants R / M_k
+    cv: np.ndarray          # [N] constant-volume specific heats
+    e0: np.ndarray          # [N] level energies, e_k(T) = e0_k + cv_k T
+    beta: np.ndarray        # [N] source weights of the reaction progress
+    ws: np.ndarray          # [N] source stoichiometry
+    K: np.ndarray           # [N][2w+1] level relaxation band, K[k][l - k + w]
+    A: float
+    theta: float
+    dt: float
+    Q: np.ndarray
+    Qn: np.ndarray
+
+    @property
+    def b(self) -> int:
+        return self.N + 3
+
+    @property
+    def n_cells(self) -> int:
+        return self.Lx * self.Ly
+
+
+def make_flow_case(Lx: int, Ly: int | None = None, N: int = 10, w: int = 2, seed: int = 0,
+                   dt: float = 0.1, mach: float = 0.4) -> FlowCase:
+    """Seeded constants and smooth state fields with 5% noise.  ``mach`` scales the
+    velocity against a sound speed near 0.7: below 1 the HLL wave-speed bounds come
+    from both sides of a face, above 1 they are clipped at zero on most faces."""
+    Ly = Lx if Ly is None else Ly
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.25, 0.45, N)
+    cv = rng.uniform(0.6, 1.2, N)
+    e0 = 0.05 * np.arange(N) + rng.uniform(0.0, 0.02, N)
+    beta = rng.uniform(0.0, 1.0, N)
+    ws = 0.1 * rng.standard_normal(N)
+    K = rng.uniform(0.0, 0.5, (N, 2 * w + 1))
+    ix, iy = np.meshgrid(np.arange(Lx), np.arange(Ly))
+    xs, ys = (ix.ravel() + 0.5) / Lx, (iy.ravel() + 0.5) / Ly
+    nc = Lx * Ly
+    Q = np.empty((nc, N + 3))
+    T = 1.0 + 0.2 * np.cos(2 * np.pi * xs) * np.sin(np.pi * ys)
+    rho = 1.0 + 0.3 * np.sin(np.pi * xs) * np.cos(np.pi * ys)
+    pop = np.exp(-np.outer(1.0 / (0.5 + 0.3 * xs), e0 / 0.05 * 0.1))
+    pop /= pop.sum(axis=1, keepdims=True)
+    Q[:, :N] = rho[:, None] * pop * (1.0 + 0.05 * rng.standard_normal((nc, N)))
+    Q[:, N] = mach * 0.7 * (1.0 + 0.3 * np.sin(2 * np.pi * ys)) * (1.0 + 0.05 * rng.standard_normal(nc))
+    Q[:, N + 1] = mach * 0.7 * 0.4 * np.cos(np.pi * xs) * (1.0 + 0.05 * rng.standard_normal(nc))
+    Q[:, N + 2] = T * (1.0 + 0.05 * rng.standard_normal(nc))
+    Qn = Q * (1.0 + 0.01 * rng.standard_normal(Q.shape))
+    return FlowCase(Lx=Lx, Ly=Ly, N=N, w=w, r=r, cv=cv, e0=e0, beta=beta, ws=ws, K=K,
+                    A=1.0, theta=2.0, dt=dt, Q=Q, Qn=Qn)
+
+
 # Workloads of the five measured configurations, named by what they are.
 WORKLOADS = {
     # 16x16 cells, N=10 (b=13), band +-2, 2 diagonal / 1 neighbour pairs, seed 0

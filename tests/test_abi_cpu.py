@@ -102,3 +102,40 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.sts_jac_destroy(None) == 0
     n = ctypes.c_size_t()
     assert lib.sts_jac_memory(None, ctypes.byref(n)) == 1
+
+
+def test_flow_create_rejects_malformed_input_on_the_host(lib):
+    c = inputs.make_flow_case(3, 2, N=4, w=1, seed=0)
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (c.r, c.cv, c.e0, c.beta, c.ws, c.K)]
+
+    def desc(**kw):
+        d = binding.sts_flow_desc()
+        d.Lx, d.Ly, d.n_species, d.band = c.Lx, c.Ly, c.N, c.w
+        d.r, d.cv, d.e0, d.beta, d.ws, d.K = [a.ctypes.data for a in keep]
+        d.A, d.theta, d.dt = c.A, c.theta, c.dt
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    def create(d):
+        h = ctypes.c_void_p()
+        st = lib.sts_flow_create(ctypes.byref(d) if d is not None else None, ctypes.byref(h))
+        return st, h, lib.sts_last_error().decode()
+
+    assert ctypes.sizeof(binding.sts_flow_desc) == 4 * 4 + 6 * 8 + 3 * 8 + 8
+    assert ctypes.sizeof(binding.sts_flow_sizes) == 6 * 4 + 8
+    st, h, msg = create(None)
+    assert st == 1 and not h.value and "desc" in msg
+    for kw, what in ((dict(Lx=0), ">= 1"), (dict(n_species=0), ">= 1"), (dict(band=-1), "band"),
+                     (dict(n_species=254), "256"), (dict(cv=None), "NULL"), (dict(dt=float("nan")), "dt")):
+        st, h, msg = create(desc(**kw))
+        assert st == 1 and not h.value and what in msg, (kw, msg)
+    bad = keep[1].copy()
+    bad[2] = 0.0
+    st, h, msg = create(desc(cv=bad.ctypes.data))
+    assert st == 1 and "cv[2]" in msg
+    for fn, args in (("sts_flow_residual", (None, None, None, None)),
+                     ("sts_flow_jacobian", (None, None, None, None, None)),
+                     ("sts_flow_get_sizes", (None, None))):
+        assert getattr(lib, fn)(*args) == 1
+    assert lib.sts_flow_destroy(None) == 0

@@ -176,27 +176,31 @@ def test_bjacobi_errors():
 # ---------------------------------------------------------------- GMRES
 
 
-@pytest.mark.parametrize("case", ["grid16_N10", "weak_diag_restart", "long_cycle", "pairs_random"])
+@pytest.mark.parametrize("case", ["grid16_N10", "weak_diag_restart", "long_cycle", "pairs_random", "left_restart"])
 def test_gmres_parity(case):
     """GMRES against the oracle's textbook GMRES.  long_cycle runs 25 Arnoldi
     steps in one cycle (no preconditioner, restart 40), so the multi-dot
     sweeps over more than one chunk of 16 basis vectors."""
-    pc = "bj"
+    pc, left = "bj", case.startswith("left")
     if case == "grid16_N10":
         w, m = workload("grid16_N10"), 20
     elif case == "weak_diag_restart":
         w, m = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 4
     elif case == "pairs_random":
         w, m = inputs.make_workload(6, 5, N=4, w=2, random_pair_max=4, seed=9, dt=0.5), 4
+    elif case == "left_restart":
+        w, m = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 4
     else:
         w, m, pc = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5), 40, "none"
     J = oracle_jac(w)
     jac = _jac(w)
     jac.bjacobi_setup()
-    xg, ig = jac.gmres(dev(w.rhs), restart=m, rtol=1e-10, history=True, precond=pc)
-    xo, io = oracle.gmres(J, w.rhs, restart=m, rtol=1e-10, precond=pc)
+    xg, ig = jac.gmres(dev(w.rhs), restart=m, rtol=1e-10, history=True, precond=pc, left=left)
+    xo, io = oracle.gmres(J, w.rhs, restart=m, rtol=1e-10, precond=pc, left=left)
     if case == "long_cycle":
         assert ig.restarts == 1 and ig.iterations > 17
+    if left:
+        assert ig.restarts > 1
     assert ig.converged and io["converged"]
     assert ig.true_rel_residual <= 1e-10 and io["true_rel"] <= 1e-10
     r = w.rhs - oracle.matvec(J, host(xg))
@@ -210,11 +214,11 @@ def test_gmres_parity(case):
     # orthogonalise differently (CGS2 here, MGS in the oracle) may differ by
     # O(eps ||b||) in the rotated residual, and that difference survives restarts
     np.testing.assert_allclose(ig.history[:n][keep], ho[:n][keep], rtol=1e-8, atol=1e-15)
-    xg2, _ = jac.gmres(dev(w.rhs), restart=m, rtol=1e-14, max_iters=400, precond=pc)
-    xo2, _ = oracle.gmres(J, w.rhs, restart=m, rtol=1e-14, max_iters=400, precond=pc)
+    xg2, _ = jac.gmres(dev(w.rhs), restart=m, rtol=1e-14, max_iters=400, precond=pc, left=left)
+    xo2, _ = oracle.gmres(J, w.rhs, restart=m, rtol=1e-14, max_iters=400, precond=pc, left=left)
     assert sol_err(host(xg2), xo2) <= TOL64
     # the reductions are deterministic: a second solve is bit-identical
-    xg3, ig3 = jac.gmres(dev(w.rhs), restart=m, rtol=1e-10, history=True, precond=pc)
+    xg3, ig3 = jac.gmres(dev(w.rhs), restart=m, rtol=1e-10, history=True, precond=pc, left=left)
     assert np.array_equal(host(xg3), host(xg)) and np.array_equal(ig3.history, ig.history)
     jac.close()
 

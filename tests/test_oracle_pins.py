@@ -361,6 +361,33 @@ def test_gmres_residual_is_krylov_least_squares():
         K.append(AM @ K[-1])
 
 
+def test_gmres_left_residual_is_krylov_least_squares():
+    """Left preconditioning (Section 6, (M A) x = M b): at step k the rotated
+    residual is min_y ||M b - M A K_k y|| over the explicit Krylov basis
+    K_k = [M b, (MA) M b, ...] (numpy lstsq), scaled by 1 / ||M b||; it never
+    grows, and the solution reaches the true residual."""
+    wl = _tiny(Lx=3, Ly=2, N=3, w=1, seed=16, dt=1.0)
+    J = oracle.Jacobian.from_workload(wl)
+    F = oracle.bj_setup(J)
+    rhs = wl.rhs
+    A = _dense_of(J)
+    Mop = np.stack([oracle.bj_apply(F, e) for e in np.eye(wl.n)], axis=1)
+    x, info = oracle.gmres(J, rhs, restart=40, rtol=1e-13, max_iters=6, factors=F, left=True)
+    hist = np.array(info["history"])
+    assert np.all(np.diff(hist) <= 1e-14)
+    MA, Mb = Mop @ A, Mop @ rhs
+    K = [Mb]
+    for k in range(1, len(hist) + 1):
+        Kk = np.stack(K, axis=1)
+        y, *_ = np.linalg.lstsq(MA @ Kk, Mb, rcond=None)
+        res = np.linalg.norm(Mb - MA @ Kk @ y) / np.linalg.norm(Mb)
+        assert abs(res - hist[k - 1]) <= 1e-8 * max(res, 1e-14), (k, res, hist[k - 1])
+        K.append(MA @ K[-1])
+    xs, its = oracle.gmres(J, rhs, restart=4, rtol=1e-12, factors=F, left=True)
+    assert its["converged"] and its["restarts"] > 1
+    np.testing.assert_allclose(xs, np.linalg.solve(A, rhs), rtol=0, atol=1e-9 * np.abs(xs).max())
+
+
 def test_gmres_finite_termination_unpreconditioned():
     """m >= n: unpreconditioned GMRES solves exactly in at most n steps."""
     wl = _tiny(Lx=2, Ly=1, N=2, w=1, seed=17, dt=1.0)
