@@ -454,6 +454,8 @@ def run_report(args):
     mixed   512x512, N=60: FP64 GMRES vs FP32/FP64 flexible GMRES, error vs the oracle;
     pairs   128x128, N=60 with the paper's pair counts (1 + 2 per face, 2 per neighbour
             block): factored vs dense matvec, apply, setup, GMRES, roofline fractions;
+    newton  128x128, N=60 HLL-flux model: residual, Jacobian generation, values update,
+            setup, GMRES, and one Newton pseudo-time step, factored vs dense;
     kernels 128x128, N=60: three rounds of FP64 and FP32 matvec and apply, a short
             fixed launch sequence for kernel profilers (no timing)."""
     import numpy as np
@@ -594,6 +596,56 @@ def run_report(args):
         print(json.dumps(out), flush=True)
         return
 
+    if args.report == "newton":
+        # one implicit pseudo-time step (Newton from Q^0 = Q^n) of the HLL-flux
+        # model, its parts timed alone, factored storage against dense BSR
+        from paper_2403_09198_gb300.binding import StsFlow
+        c = inputs.make_flow_case(128, 128, N=60, w=2, seed=13, dt=0.5)
+        f = StsFlow(c)
+        L, z = f.layout, f.sizes
+        Q, Qn = t(c.Q), t(c.Qn)
+        R = torch.empty_like(Q)
+        S, U, V = f.jacobian(Q)
+        gen_bytes = 8 * (z.nnz_S + 2 * z.n_pairs * z.block_size + 6 * z.n_cells * z.block_size)
+        out = {"report": "newton",
+               "workload": "flow128_N60: 128x128 cells, N=60 species, b=63, band +-2, dt=0.5, "
+                           "1 + 2 pairs per face on diagonal blocks, 2 per neighbour block",
+               "residual_ms": avg(lambda: f.residual(Q, Qn, out=R), 50),
+               "jacobian_ms": avg(lambda: f.jacobian(Q, S, U, V), 20),
+               "jacobian_written_bytes": gen_bytes}
+        out["jacobian_GBps"] = gen_bytes / (out["jacobian_ms"] * 1e-3) / 1e9
+        rhs = -f.residual(Q, Qn).reshape(-1)
+        for name, kw in (("factored", {}), ("dense", {"dense": True})):
+            jac = f.jacobian_handle(Q=Q, **kw)
+            r = {"update_values_ms": avg(lambda: jac.update_values(S, U, V), 3 if kw else 10)}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            jac.bjacobi_setup()
+            r["setup_ms"] = 1e3 * (time.perf_counter() - t0)
+            jac.gmres(rhs, rtol=1e-10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, gi = jac.gmres(rhs, rtol=1e-10)
+            r["gmres_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["gmres_iterations"] = gi.iterations
+            Qs = Qn.clone()
+            f.newton(jac, Qs, Qn, rtol=1e-10)           # warm-up of the whole step
+            Qs = Qn.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info, hist = f.newton(jac, Qs, Qn, rtol=1e-10)
+            r["newton_step_ms"] = 1e3 * (time.perf_counter() - t0)
+            r["newton"] = {k: info[k] for k in ("iterations", "linear_iterations", "halvings", "res0", "res")}
+            r["residual_history"] = hist.tolist()
+            r["memory_GB"] = jac.memory_bytes() / 1e9
+            out[name] = r
+            jac.close()
+            torch.cuda.empty_cache()
+        out["speedup_newton_step"] = out["dense"]["newton_step_ms"] / out["factored"]["newton_step_ms"]
+        f.close()
+        print(json.dumps(out), flush=True)
+        return
+
     if args.report == "mixed":
         import oracle
         oracle.build()
@@ -659,7 +711,7 @@ def main():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels", "pairs"], default=None,
+    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels", "pairs", "newton"], default=None,
                    help="print an extra measurement instead of the benchmark line")
     args = p.parse_args()
     if args.report:

@@ -383,8 +383,8 @@ sts_status sts_flow_destroy(sts_flow_t f);
  * at 1 and is halved while ||R|| does not decrease, at most max_halvings times.
  * A linear solve that stops at max_iters without converging still gives a step
  * (inexact Newton).  Stops when ||R(Q)||_2 <= max(rtol ||R(Q^0)||, atol).
- *   jac: a factored handle created from this generator's layout
- *        (sts_flow_get_layout), vec_layout STS_LAYOUT_CELL_MAJOR; its values are
+ *   jac: a handle created from this generator's layout (sts_flow_get_layout),
+ *        vec_layout STS_LAYOUT_CELL_MAJOR, factored or dense-BSR; its values are
  *        overwritten.
  *   Q: DEVICE [n_cells][b], the initial iterate on entry, the result on exit;
  *   Qn: DEVICE, the previous time level.

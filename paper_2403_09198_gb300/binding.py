@@ -402,9 +402,9 @@ class StsFlow:
         return S, U, V
 
     def jacobian_handle(self, **kw):
-        """A factored, cell-major ``StsJacobian`` of this layout (values of the
-        flow Jacobian at the states ``kw.pop('Q')`` if given, else zeros with
-        unit S diagonal-free placeholders), for ``newton``."""
+        """A cell-major ``StsJacobian`` of this layout for ``newton`` (``dense=True``
+        for the dense-BSR storage), holding the flow Jacobian at the states
+        ``Q=...`` if given, else zeros (``newton`` writes its own values)."""
         import torch
         Q = kw.pop("Q", None)
         if Q is None:

@@ -8,11 +8,19 @@
 // scalars and takes the same wave-speed branch.  Per face the warp forms the
 // HLL bounds s_L, s_R, the coefficients a_f, c_f and their gradients, writes the
 // face's two rank-one pairs into the diagonal block of its cell and into the
-// neighbour block, and the neighbour block's sparse part dt A0_R on the
-// neighbour pattern; the diagonal block's sparse part H + dt (sum A0_L + K) is
-// written last.  Lanes stride over pattern entries and vector components.
-// Every face is evaluated from both of its cells (once per block row), which
-// keeps the writes of a block row in one warp: no atomics, deterministic.
+// neighbour block, and the neighbour block's sparse part dt A0_R; the diagonal
+// block's sparse part H + dt (sum A0_L + K) is written last.  Every face is
+// evaluated from both of its cells (once per block row), which keeps the writes
+// of a block row in one warp: no atomics, deterministic.
+//
+// These kernels are bound by the FP64 pipe (a warp-wide FP64 instruction holds
+// a sub-partition's pipe for 64 cycles), so the FP64 work per entry is kept
+// small.  A_n is linear in the normal, so the diagonal block's face sum
+// sum_f (1/2 + a_f) A_{n_f}(q_i) is A_n(q_i) at the summed normal.  Level rows,
+// whose entries of A_n and H are u_n, rho_p n and 1, are written from four
+// per-face coefficient sums with lanes over rows; only the three dense flow rows
+// evaluate A_n and H entry by entry (lanes over columns), once per block;
+// reciprocals are formed once per face and per state, not per component.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,11 +41,12 @@ struct FlowDev {
     double A, theta, dt;
     const int *bptr, *bidx, *pip;
     const long long *soff;
-    const int *d_row, *d_col, *o_row, *o_col;
+    const int *d_ptr;       // row starts of the diagonal pattern (the neighbour pattern's are 4p, then 4N + b (p-N))
 };
 
 struct Mix {
     double rho, Rt, Ct, E0, u, v, T, ke, p, rhoetot, g, a;
+    double cga, gaT;        // T / (2 a rho C) and a / (2 T): the factors of da/dq
 };
 
 // Sum over the warp, the same value on every lane (tree to lane 0, then broadcast).
@@ -69,6 +78,8 @@ __device__ Mix mixture(const FlowDev &F, const double *q, int lane) {
     m.rhoetot = m.E0 + m.Ct * m.T + m.rho * m.ke;
     m.g = (m.Ct + m.Rt) * m.Rt / (m.rho * m.Ct);
     m.a = sqrt(m.g * m.T);
+    m.cga = m.T / (2.0 * m.a * m.rho * m.Ct);
+    m.gaT = m.a / (2.0 * m.T);
     return m;
 }
 
@@ -132,16 +143,15 @@ __device__ double An_e(const FlowDev &F, const double *q, const Mix &m, double n
 // component c of da/dq: a^2 = T g, g = (C + R) R / (rho C)
 __device__ double grad_a_c(const FlowDev &F, const Mix &m, int c) {
     if (c < F.N) {
-        const double d = m.rho * m.Ct;
         const double dn = (F.cv[c] + F.r[c]) * m.Rt + (m.Ct + m.Rt) * F.r[c];
         const double dd = m.Ct + m.rho * F.cv[c];
-        return m.T / (2.0 * m.a) * (dn - m.g * dd) / d;
+        return m.cga * (dn - m.g * dd);
     }
-    return c == F.N + 2 ? m.a / (2.0 * m.T) : 0.0;
+    return c == F.N + 2 ? m.gaT : 0.0;
 }
 
 struct Face {
-    double nx, ny, sL, sR, af, cf, den2;
+    double nx, ny, sL, sR, af, cf, inv_den, inv_den2;
     int iL, iR;
 };
 
@@ -159,10 +169,14 @@ __device__ Face face_of(const Mix &mL, const Mix &mR, double nx, double ny) {
     f.iR = 0;
     if (unL + mL.a > f.sR) { f.sR = unL + mL.a; f.iR = 1; }
     if (unR + mR.a > f.sR) { f.sR = unR + mR.a; f.iR = 2; }
+    // a_f and c_f by division: on a supersonic face a_f is exactly +-1/2 and the
+    // upwind side's weight 1/2 -+ a_f exactly zero; the per-component products
+    // use the reciprocal
     const double den = f.sR - f.sL;
     f.af = 0.5 * (f.sL + f.sR) / den;
     f.cf = f.sL * f.sR / den;
-    f.den2 = den * den;
+    f.inv_den = 1.0 / den;
+    f.inv_den2 = f.inv_den * f.inv_den;
     return f;
 }
 
@@ -181,7 +195,7 @@ __global__ void __launch_bounds__(kFlowWarps * 32) k_flow_jac(FlowDev F, const d
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFlowWarps + (threadIdx.x >> 5);
     if (i >= F.nc) return;
-    const int b = F.b, N = F.N;
+    const int b = F.b, N = F.N, w = F.w;
     const double dt = F.dt;
     const double *qi = Q + (size_t)i * b;
     const Mix mi = mixture(F, qi, lane);
@@ -189,8 +203,10 @@ __global__ void __launch_bounds__(kFlowWarps * 32) k_flow_jac(FlowDev F, const d
     int kd = k0;
     for (int k = k0; k < k1; ++k)
         if (F.bidx[k] == i) kd = k;
-    Face fc[4];
     int nf = 0;
+    // sums over the faces for the diagonal block:
+    // sum (1/2 + a_f) u_n(q_i), sum c_f, sum (1/2 + a_f) n_x, sum (1/2 + a_f) n_y
+    double cun = 0.0, ccf = 0.0, cnx = 0.0, cny = 0.0;
     for (int k = k0; k < k1 && nf < 4; ++k) {
         const int j = F.bidx[k];
         if (j == i) continue;
@@ -199,13 +215,25 @@ __global__ void __launch_bounds__(kFlowWarps * 32) k_flow_jac(FlowDev F, const d
         double nx, ny;
         normal_of(F.Lx, i, j, nx, ny);
         const Face f = face_of(mi, mj, nx, ny);
-        fc[nf] = f;
-        // neighbour block: dt A0_R on the neighbour pattern
-        const double cR = 0.5 - f.af;
+        const double wL = 0.5 + f.af, wR = 0.5 - f.af;
+        cun += wL * (nx * mi.u + ny * mi.v);
+        ccf += f.cf;
+        cnx += wL * nx;
+        cny += wL * ny;
+        // neighbour block dt A0_R = dt ((1/2 - a_f) A_n(q_j) + c_f H(q_j)):
+        // level row p holds (p, p) = u_n(q_j) and 1, (p, N) = rho_p n_x, (p, N+1) = rho_p n_y, (p, N+2) = 0
         double *Sk = S + F.soff[k];
-        for (int e = lane; e < F.nnz_o; e += 32) {
-            const int p = F.o_row[e], c = F.o_col[e];
-            Sk[e] = dt * (cR * An_e(F, qj, mj, nx, ny, p, c) + f.cf * H_e(F, mj, p, c));
+        const double unj = nx * mj.u + ny * mj.v;
+        for (int p = lane; p < N; p += 32) {
+            const double wq = wR * qj[p];
+            Sk[4 * p] = dt * (wR * unj + f.cf);
+            Sk[4 * p + 1] = dt * (wq * nx);
+            Sk[4 * p + 2] = dt * (wq * ny);
+            Sk[4 * p + 3] = 0.0;
+        }
+        for (int e = lane; e < 3 * b; e += 32) {
+            const int p = N + e / b, c = e - (e / b) * b;
+            Sk[4 * N + e] = dt * (wR * An_e(F, qj, mj, nx, ny, p, c) + f.cf * H_e(F, mj, p, c));
         }
         // the face's two pairs: into the diagonal block (d/dq_i) and the neighbour block (d/dq_j)
         const size_t pd = (size_t)(F.pip[kd] + 1 + 2 * nf), po = (size_t)F.pip[k];
@@ -217,36 +245,50 @@ __global__ void __launch_bounds__(kFlowWarps * 32) k_flow_jac(FlowDev F, const d
             const double dsLL = f.iL == 1 ? gun - gaL : 0.0, dsLR = f.iL == 2 ? gun - gaR : 0.0;
             const double dsRL = f.iR == 1 ? gun + gaL : 0.0, dsRR = f.iR == 2 ? gun + gaR : 0.0;
             U[pd * b + c] = dt * u1;
-            V[pd * b + c] = (f.sR * dsLL - f.sL * dsRL) / f.den2;
+            V[pd * b + c] = (f.sR * dsLL - f.sL * dsRL) * f.inv_den2;
             U[(pd + 1) * b + c] = dt * u2;
-            V[(pd + 1) * b + c] = (f.sR * f.sR * dsLL - f.sL * f.sL * dsRL) / f.den2;
+            V[(pd + 1) * b + c] = (f.sR * f.sR * dsLL - f.sL * f.sL * dsRL) * f.inv_den2;
             U[po * b + c] = dt * u1;
-            V[po * b + c] = (f.sR * dsLR - f.sL * dsRR) / f.den2;
+            V[po * b + c] = (f.sR * dsLR - f.sL * dsRR) * f.inv_den2;
             U[(po + 1) * b + c] = dt * u2;
-            V[(po + 1) * b + c] = (f.sR * f.sR * dsLR - f.sL * f.sL * dsRR) / f.den2;
+            V[(po + 1) * b + c] = (f.sR * f.sR * dsLR - f.sL * f.sL * dsRR) * f.inv_den2;
         }
         ++nf;
     }
-    // diagonal block: H(q_i) + dt K + sum over faces dt A0_L on the diagonal pattern
+    // diagonal block H(q_i) + dt K + sum over faces dt A0_L: level row p holds the
+    // band (K, plus H = 1 and the face terms on the diagonal), then (p, N), (p, N+1), (p, N+2)
     double *Sd = S + F.soff[kd];
-    for (int e = lane; e < F.nnz_d; e += 32) {
-        const int p = F.d_row[e], c = F.d_col[e];
+    for (int p = lane; p < N; p += 32) {
+        double *row = Sd + F.d_ptr[p];
+        const int c0 = max(0, p - w), c1 = min(N - 1, p + w);
+        const double *Kp = F.K + (size_t)p * (2 * w + 1) - p + w;      // Kp[c] = K[p][c - p + w]
+        for (int c = c0; c <= c1; ++c) {
+            const double kb = dt * Kp[c];
+            row[c - c0] = c == p ? (1.0 + kb) + dt * (cun - ccf) : kb;
+        }
+        const double qp = dt * qi[p];
+        row[c1 - c0 + 1] = qp * cnx;
+        row[c1 - c0 + 2] = qp * cny;
+        row[c1 - c0 + 3] = 0.0;
+    }
+    // flow rows: A_n is linear in n, so sum_f (1/2 + a_f) A_{n_f}(q_i) = A_{(cnx, cny)}(q_i)
+    // (K is zero on the flow rows)
+    double *Sf = Sd + F.d_ptr[N];
+    for (int e = lane; e < 3 * b; e += 32) {
+        const int p = N + e / b, c = e - (e / b) * b;
         const double h = H_e(F, mi, p, c);
-        const double kb = (p < N && c < N && abs(c - p) <= F.w) ? F.K[(size_t)p * (2 * F.w + 1) + (c - p + F.w)] : 0.0;
-        double val = h - dt * (-kb);
-        for (int t = 0; t < nf; ++t)
-            val += dt * ((0.5 + fc[t].af) * An_e(F, qi, mi, fc[t].nx, fc[t].ny, p, c) - fc[t].cf * h);
-        Sd[e] = val;
+        Sf[e] = h + dt * (An_e(F, qi, mi, cnx, cny, p, c) - ccf * h);
     }
     // source pair (-dt ws, d omega / dq)
     double sb = 0.0;
     for (int k = lane; k < N; k += 32) sb += F.beta[k] * qi[k];
     sb = warp_total(sb);
     const double kap = F.A * exp(-F.theta / mi.T);
+    const double kT = kap * F.theta / (mi.T * mi.T) * sb;
     const size_t ps = (size_t)F.pip[kd];
     for (int c = lane; c < b; c += 32) {
         U[ps * b + c] = c < N ? -dt * F.ws[c] : 0.0;
-        V[ps * b + c] = c < N ? kap * F.beta[c] : c == N + 2 ? kap * F.theta / (mi.T * mi.T) * sb : 0.0;
+        V[ps * b + c] = c < N ? kap * F.beta[c] : c == N + 2 ? kT : 0.0;
     }
 }
 
@@ -282,7 +324,7 @@ __global__ void __launch_bounds__(kFlowWarps * 32) k_flow_res(FlowDev F, const d
             if (c < b) {
                 const double fL = flux_c(F, qi, mi, nx, ny, c), fR = flux_c(F, qj, mj, nx, ny, c);
                 const double uL = cons_c(F, qi, mi, c), uR = cons_c(F, qj, mj, c);
-                fsum[t] = fsum[t] + (f.sR * fL - f.sL * fR + f.sL * f.sR * (uR - uL)) / (f.sR - f.sL);
+                fsum[t] = fsum[t] + (f.sR * fL - f.sL * fR + f.sL * f.sR * (uR - uL)) * f.inv_den;
             }
         }
     }
@@ -390,10 +432,10 @@ sts_status flow_newton(sts_flow_s *f, sts_jac_t jac, double *Q, const double *Qn
     if (d.gmres.vectors_on_host) return set_error(STS_ERR_INVALID_ARG, "sts_flow_newton: gmres.vectors_on_host must be 0");
     if (d.gmres.trans) return set_error(STS_ERR_INVALID_ARG, "sts_flow_newton: gmres.trans must be 0");
     // the handle must hold this generator's layout
-    if (jac->rep != STS_REP_FACTORED || jac->layout != STS_LAYOUT_CELL_MAJOR || jac->nc != f->dev.nc ||
+    if (jac->layout != STS_LAYOUT_CELL_MAJOR || jac->nc != f->dev.nc ||
         jac->b != f->dev.b || jac->bidx != f->bidx || jac->bptr != f->bptr || jac->pbase != f->pip ||
         jac->dptr != f->dptr || jac->didx != f->didx || jac->optr != f->optr || jac->oidx != f->oidx)
-        return set_error(STS_ERR_INVALID_ARG, "sts_flow_newton: jac is not a factored, cell-major handle of this "
+        return set_error(STS_ERR_INVALID_ARG, "sts_flow_newton: jac is not a cell-major handle of this "
                                               "generator's layout");
     const long long n = (long long)f->dev.nc * f->dev.b;
     if (!f->R) {
@@ -532,8 +574,7 @@ sts_status flow_create(const sts_flow_desc *d, sts_flow_t *out) {
         if (iy < Ly - 1) f->bidx.push_back(i + Lx);
         f->bptr.push_back((int)f->bidx.size());
     }
-    // patterns
-    std::vector<int> drow, orow;
+    // patterns (the kernels write them in this order)
     f->dptr.assign(1, 0);
     f->optr.assign(1, 0);
     for (int p = 0; p < b; ++p) {
@@ -548,8 +589,6 @@ sts_status flow_create(const sts_flow_desc *d, sts_flow_t *out) {
                 f->oidx.push_back(c);
             }
         }
-        drow.resize(f->didx.size(), p);
-        orow.resize(f->oidx.size(), p);
         f->dptr.push_back((int)f->didx.size());
         f->optr.push_back((int)f->oidx.size());
     }
@@ -589,10 +628,7 @@ sts_status flow_create(const sts_flow_desc *d, sts_flow_t *out) {
         if ((st = flow_upload(f, &D.bidx, f->bidx.data(), f->bidx.size())) != STS_OK) break;
         if ((st = flow_upload(f, &D.pip, f->pip.data(), f->pip.size())) != STS_OK) break;
         if ((st = flow_upload(f, &D.soff, soff.data(), soff.size())) != STS_OK) break;
-        if ((st = flow_upload(f, &D.d_row, drow.data(), drow.size())) != STS_OK) break;
-        if ((st = flow_upload(f, &D.d_col, f->didx.data(), f->didx.size())) != STS_OK) break;
-        if ((st = flow_upload(f, &D.o_row, orow.data(), orow.size())) != STS_OK) break;
-        if ((st = flow_upload(f, &D.o_col, f->oidx.data(), f->oidx.size())) != STS_OK) break;
+        if ((st = flow_upload(f, &D.d_ptr, f->dptr.data(), f->dptr.size())) != STS_OK) break;
         cudaError_t e = cudaStreamSynchronize(f->stream);   // the host vectors above are temporaries
         if (e != cudaSuccess) st = set_error(STS_ERR_CUDA, "sts_flow_create: %s", cudaGetErrorString(e));
     } while (false);
