@@ -2,11 +2,13 @@
 // (Section 6).  Each diagonal block is A_k = A_k^0 + U_k V_k^T with A_k^0 = S_kk
 // sparse (Eq. R1_Block_Jacobian).
 //
-// Setup, one thread per cell (lane = cell, all cells share one schedule):
+// Setup (all cells share one schedule; thread index = cell, fastest):
 //   LU of A_k^0 without pivoting on the symbolic schedule of the shared
 //   pattern (natural order; for the paper's arrow pattern there is no fill),
-//   W_k = (A_k^0)^-1 U_k   (SMW-1, r sparse solves),
-//   C_k = I + V_k^T W_k    (FP64), C_k^-1 by Gauss-Jordan with pivoting.
+//   one thread per cell;
+//   W_k = (A_k^0)^-1 U_k   (SMW-1, r sparse solves), one thread per solve;
+//   C_k = I + V_k^T W_k    (FP64), C_k^-1 by Gauss-Jordan with pivoting, one
+//   thread per cell.
 // Apply (SMW-1..3): x0 = (A_k^0)^-1 b_k, t = V_k^T x0, z = C_k^-1 t (FP64),
 //   x_k = x0 - W_k z.  The paper prints "+ W_k z"; with C_k = I + V^T A0^-1 U the
 //   Woodbury identity needs the minus sign, which is what is computed here.
@@ -72,30 +74,22 @@ __device__ void lu_solve_T(const SetupArgs &a, double *w, int cell) {
     }
 }
 
-__global__ void k_smw_setup(SetupArgs a) {
+// Setup step 1, one thread per cell: the static-pivot LU of S_kk on the shared
+// schedule.  A padding cell gets the identity, so steps 2 and 3 give it W = 0 and
+// C^-1 = I without a special case.
+__global__ void k_smw_lu(SetupArgs a) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= a.ncp) return;
     const size_t P = a.ncp;
-    const int r = a.r;
-    if (cell >= a.nc) {   // padding cell: identity block, no pairs
-        for (int s = 0; s < a.nnz_lu; ++s) a.lu[s * P + cell] = 0.0;
+    for (int s = 0; s < a.nnz_lu; ++s) a.lu[s * P + cell] = 0.0;
+    if (cell >= a.nc) {
         for (int i = 0; i < a.b; ++i) {
             a.lu[(size_t)a.lu_diag[i] * P + cell] = 1.0;
             a.dinv[i * P + cell] = 1.0;
         }
-        for (int k = 0; k < r; ++k)
-            for (int q = 0; q < a.b; ++q) {
-                a.W[((size_t)k * a.b + q) * P + cell] = 0.0;
-                if (a.with_T) a.Wt[((size_t)k * a.b + q) * P + cell] = 0.0;
-            }
-        for (int k = 0; k < r; ++k)
-            for (int l = 0; l < r; ++l) a.Cinv[((size_t)k * r + l) * P + cell] = k == l ? 1.0 : 0.0;
         return;
     }
-    // 1. load S_kk into the LU slots
-    for (int s = 0; s < a.nnz_lu; ++s) a.lu[s * P + cell] = 0.0;
     for (int e = 0; e < a.nnz_d; ++e) a.lu[(size_t)a.src_slot[e] * P + cell] = a.Sd[e * P + cell];
-    // 2. static-pivot LU on the shared schedule
     for (int k = 0; k < a.b; ++k) {
         double rowmax = 0.0;
         for (int e = a.d_ptr[k]; e < a.d_ptr[k + 1]; ++e) rowmax = fmax(rowmax, fabs(a.Sd[e * P + cell]));
@@ -115,18 +109,33 @@ __global__ void k_smw_setup(SetupArgs a) {
                     fma(-l, a.lu[(size_t)a.upd_src[u] * P + cell], a.lu[(size_t)a.upd_tgt[u] * P + cell]);
         }
     }
-    // 3. W = A0^-1 U (SMW-1) and, for the adjoint, Wt = A0^-T V
-    for (int k = 0; k < r; ++k) {
-        double *w = a.W + (size_t)k * a.b * P;
-        for (int q = 0; q < a.b; ++q) w[q * P + cell] = a.Ud[((size_t)k * a.b + q) * P + cell];
-        lu_solve_N(a, w, cell);
-        if (a.with_T) {
-            double *wt = a.Wt + (size_t)k * a.b * P;
-            for (int q = 0; q < a.b; ++q) wt[q * P + cell] = a.Vd[((size_t)k * a.b + q) * P + cell];
-            lu_solve_T(a, wt, cell);
-        }
-    }
-    // 4. C = I + V^T W (FP64) and its inverse (Gauss-Jordan, partial pivoting)
+}
+
+// Setup step 2, one thread per (cell, pair k, direction): W_k = A0^-1 U_k (SMW-1)
+// and, for the adjoint, Wt_k = A0^-T V_k.  Consecutive threads take consecutive
+// cells, so every [slot][cell] access of a warp is one coalesced request.
+__global__ void k_smw_w(SetupArgs a) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_dir = (long long)a.ncp * a.r;
+    if (t >= per_dir * (a.with_T ? 2 : 1)) return;
+    const int dir = (int)(t / per_dir);
+    const long long u = t - dir * per_dir;
+    const int k = (int)(u / a.ncp), cell = (int)(u - (long long)k * a.ncp);
+    const size_t P = a.ncp;
+    double *w = (dir ? a.Wt : a.W) + (size_t)k * a.b * P;
+    const double *src = (dir ? a.Vd : a.Ud) + (size_t)k * a.b * P;
+    for (int q = 0; q < a.b; ++q) w[q * P + cell] = src[q * P + cell];
+    if (dir) lu_solve_T(a, w, cell);
+    else lu_solve_N(a, w, cell);
+}
+
+// Setup step 3, one thread per cell: C = I + V^T W (FP64) and its inverse
+// (Gauss-Jordan, partial pivoting).
+__global__ void k_smw_cinv(SetupArgs a) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= a.ncp) return;
+    const size_t P = a.ncp;
+    const int r = a.r;
     double C[kMaxPairsDiag][kMaxPairsDiag], X[kMaxPairsDiag][kMaxPairsDiag];
     double cmax = 0.0;
     for (int k = 0; k < r; ++k)
@@ -1065,7 +1074,14 @@ sts_status smw_setup(sts_jac_s *h) {
     a.nnz_d = h->nnz_d; a.with_T = h->has_T ? 1 : 0;
     const int big = INT_MAX;
     STS_CK(cudaMemcpyAsync(M.err_cell, &big, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    k_smw_setup<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
+    k_smw_lu<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
+    STS_LAUNCHED();
+    const long long nw = (long long)h->ncp * a.r * (a.with_T ? 2 : 1);
+    if (nw > 0) {
+        k_smw_w<<<(unsigned)((nw + 63) / 64), 64, 0, h->stream>>>(a);
+        STS_LAUNCHED();
+    }
+    k_smw_cinv<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
     STS_LAUNCHED();
     int bad = INT_MAX;
     STS_CK(cudaMemcpyAsync(&bad, M.err_cell, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

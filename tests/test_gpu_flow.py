@@ -110,18 +110,19 @@ def test_flow_rejects_bad_constants():
     assert e.value.status == 1 and "r[1]" in e.value.message
 
 
-@pytest.mark.parametrize("left", [False, True])
-def test_newton_step_matches_oracle_root(left):
-    """sts_flow_newton from Q^0 = Q^n: converges in as many iterations as the
-    oracle's dense Newton (+-1), quadratically at the end, to the same root
-    (1e-9 relative, both residuals driven to ~1e-13 of the start)."""
+@pytest.mark.parametrize("variant", ["right", "left", "dense"])
+def test_newton_step_matches_oracle_root(variant):
+    """sts_flow_newton from Q^0 = Q^n (right or left block-Jacobi GMRES, or the
+    dense-BSR storage): converges in as many iterations as the oracle's dense
+    Newton (+-1), quadratically at the end, to the same root (1e-9 relative,
+    both residuals driven to ~1e-13 of the start)."""
     c = inputs.make_flow_case(6, 5, N=5, w=1, seed=12, dt=2.0)
     m = flux.model_of(c)
     Qo, ho = flux.newton(m, c.Lx, c.Ly, c.Qn, c.Qn, rtol=1e-13)
     f = StsFlow(c)
-    jac = f.jacobian_handle()
+    jac = f.jacobian_handle(dense=variant == "dense")
     Q = dev(c.Qn.copy())
-    info, hist = f.newton(jac, Q, dev(c.Qn), rtol=1e-12, gmres_rtol=1e-13, left=left)
+    info, hist = f.newton(jac, Q, dev(c.Qn), rtol=1e-12, gmres_rtol=1e-13, left=variant == "left")
     assert info["converged"] and info["res"] <= 1e-12 * info["res0"]
     assert abs(info["iterations"] - (len(ho) - 1)) <= 1
     assert abs(hist[0] - ho[0]) <= 1e-12 * ho[0]
