@@ -7,8 +7,8 @@
 //   pattern (natural order; for the paper's arrow pattern there is no fill),
 //   one thread per cell;
 //   W_k = (A_k^0)^-1 U_k   (SMW-1, r sparse solves), one thread per solve;
-//   C_k = I + V_k^T W_k    (FP64), C_k^-1 by Gauss-Jordan with pivoting, one
-//   thread per cell.
+//   C_k = I + V_k^T W_k    (FP64), one thread per entry; C_k^-1 by Gauss-Jordan
+//   with pivoting, one thread per cell.
 // Apply (SMW-1..3): x0 = (A_k^0)^-1 b_k, t = V_k^T x0, z = C_k^-1 t (FP64),
 //   x_k = x0 - W_k z.  The paper prints "+ W_k z"; with C_k = I + V^T A0^-1 U the
 //   Woodbury identity needs the minus sign, which is what is computed here.
@@ -129,8 +129,23 @@ __global__ void k_smw_w(SetupArgs a) {
     else lu_solve_N(a, w, cell);
 }
 
-// Setup step 3, one thread per cell: C = I + V^T W (FP64) and its inverse
-// (Gauss-Jordan, partial pivoting).
+// Setup step 3a, one thread per (cell, k, l): C_kl = delta_kl + V_k . W_l (FP64),
+// written into the C^-1 array, which step 3b inverts in place.
+__global__ void k_smw_cmat(SetupArgs a) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = a.r;
+    if (t >= (long long)a.ncp * r * r) return;
+    const int kl = (int)(t / a.ncp), cell = (int)(t - (long long)kl * a.ncp);
+    const int k = kl / r, l = kl - k * r;
+    const size_t P = a.ncp;
+    const double *v = a.Vd + (size_t)k * a.b * P + cell, *w = a.W + (size_t)l * a.b * P + cell;
+    double acc = k == l ? 1.0 : 0.0;
+    for (int q = 0; q < a.b; ++q) acc = fma(v[q * P], w[q * P], acc);
+    a.Cinv[(size_t)kl * P + cell] = acc;
+}
+
+// Setup step 3b, one thread per cell: C^-1 by Gauss-Jordan with partial pivoting,
+// in place in the C^-1 array.
 __global__ void k_smw_cinv(SetupArgs a) {
     const int cell = blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= a.ncp) return;
@@ -140,12 +155,9 @@ __global__ void k_smw_cinv(SetupArgs a) {
     double cmax = 0.0;
     for (int k = 0; k < r; ++k)
         for (int l = 0; l < r; ++l) {
-            double acc = k == l ? 1.0 : 0.0;
-            for (int q = 0; q < a.b; ++q)
-                acc = fma(a.Vd[((size_t)k * a.b + q) * P + cell], a.W[((size_t)l * a.b + q) * P + cell], acc);
-            C[k][l] = acc;
+            C[k][l] = a.Cinv[((size_t)k * r + l) * P + cell];
             X[k][l] = k == l ? 1.0 : 0.0;
-            cmax = fmax(cmax, fabs(acc));
+            cmax = fmax(cmax, fabs(C[k][l]));
         }
     for (int k = 0; k < r; ++k) {
         int pr = k;
@@ -1080,9 +1092,12 @@ sts_status smw_setup(sts_jac_s *h) {
     if (nw > 0) {
         k_smw_w<<<(unsigned)((nw + 63) / 64), 64, 0, h->stream>>>(a);
         STS_LAUNCHED();
+        const long long nc2 = (long long)h->ncp * a.r * a.r;
+        k_smw_cmat<<<(unsigned)((nc2 + 255) / 256), 256, 0, h->stream>>>(a);
+        STS_LAUNCHED();
+        k_smw_cinv<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
+        STS_LAUNCHED();
     }
-    k_smw_cinv<<<(h->ncp + 63) / 64, 64, 0, h->stream>>>(a);
-    STS_LAUNCHED();
     int bad = INT_MAX;
     STS_CK(cudaMemcpyAsync(&bad, M.err_cell, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     STS_CK(cudaStreamSynchronize(h->stream));
