@@ -384,16 +384,27 @@ class StsFlow:
         except Exception:
             pass
 
+    def _states(self, *ts):
+        import torch
+        n = self.sizes.n_cells * self.sizes.block_size
+        for t in ts:
+            if (not torch.is_tensor(t) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous()
+                    or t.numel() != n):
+                raise ValueError(f"states must be contiguous float64 CUDA tensors of {n} values")
+
     def residual(self, Q, Qn, out=None):
         """R(Q) given the previous level Qn; CUDA float64 tensors [n_cells, b]."""
         import torch
+        self._states(Q, Qn)
         R = torch.empty_like(Q) if out is None else out
+        self._states(R)
         check(self.lib.sts_flow_residual(self.h, _ptr(Q), _ptr(Qn), _ptr(R)))
         return R
 
     def jacobian(self, Q, S=None, U=None, V=None):
         """(S, U, V) of dR/dQ at Q in ``self.layout``; CUDA float64 tensors."""
         import torch
+        self._states(Q)
         z, dev = self.sizes, Q.device
         S = torch.empty(z.nnz_S, dtype=torch.float64, device=dev) if S is None else S
         U = torch.empty((z.n_pairs, z.block_size), dtype=torch.float64, device=dev) if U is None else U
@@ -421,6 +432,7 @@ class StsFlow:
                precond: str = "bj", left: bool = False, raise_on_fail: bool = True):
         """One pseudo-time step by Newton's method; Q (CUDA [n_cells, b]) is updated
         in place.  Returns (info dict, history of ||R||)."""
+        self._states(Q, Qn)
         o = sts_newton_opts()
         o.max_newton, o.rtol, o.atol, o.max_halvings = max_newton, rtol, atol, max_halvings
         o.gmres.restart, o.gmres.max_iters, o.gmres.rtol = restart, gmres_max_iters, gmres_rtol

@@ -36,6 +36,8 @@ CASES = {
     "row7x1": dict(Lx=7, Ly=1, N=4, w=2, seed=5),
     "grid16_N20": dict(Lx=16, Ly=16, N=20, w=2, seed=6),
     "N40_b43": dict(Lx=3, Ly=2, N=40, w=3, seed=7),
+    "N1_single_species": dict(Lx=3, Ly=3, N=1, w=0, seed=8),
+    "band_wider_than_levels": dict(Lx=3, Ly=2, N=2, w=3, seed=9),
 }
 
 
