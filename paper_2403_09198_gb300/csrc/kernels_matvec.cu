@@ -567,10 +567,30 @@ void (*mv_struct_kernel(int nreg))(MvArgs<T>) {
     return nreg == 8 ? k_mv_struct<T, WD, 8> : nreg ? k_mv_struct<T, WD, 2 * kStructDuff> : k_mv_struct<T, WD, 0>;
 }
 
+// Level rows per pass-2 item.  The persistent grid deals the n_tiles x (groups +
+// 1) items round-robin to W resident warps, so its last round runs partly full.
+// With few rounds, take the group size of 4..8 rows whose last round is fullest
+// (the plan's size unless another fills strictly more); measured on 128 x 128
+// cells, N = 60: 4 rows (last round 85% full) 109.7 us against 111.0 us at 6
+// rows (65%); with 9 diagonal pairs, 6 rows (70%) 154.6 us against 158.0 us at 4.
+inline int pass2_group_rows(int N, int n_tiles, long long W, int s_plan) {
+    auto items = [&](int s) { return (long long)n_tiles * ((N + s - 1) / s + 1); };
+    auto fill = [&](int s) {
+        const long long r = items(s) % W;
+        return r == 0 ? 1.0 : (double)r / (double)W;
+    };
+    if (W <= 0 || items(s_plan) >= 8 * W) return s_plan;
+    int best = s_plan;
+    for (int s = 8; s >= 4; --s)
+        if (s <= N && fill(s) > fill(best) + 1e-9) best = s;
+    return best;
+}
+
 template <typename T>
-sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
-    STS_TRY(dots_launch<T>(h, a));
-    const long long warps = (long long)a.n_tiles * a.n_groups;
+sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &args) {
+    STS_TRY(dots_launch<T>(h, args));
+    MvArgs<T> a = args;
+    long long warps = (long long)a.n_tiles * a.n_groups;
     const unsigned grid = (unsigned)((warps + 3) / 4);
     if (a.structured) {
         constexpr int kWarpsPerBlock = 2;      // two row stages per warp; small blocks pack the SM finely
@@ -592,6 +612,10 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &a) {
             STS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * kTile, smem));
             resident = std::max(per_sm, 1) * h->nsm;
         }
+        a.s_gl = pass2_group_rows(a.sN, a.n_tiles, (long long)resident * kWarpsPerBlock, a.s_gl);
+        a.n_lgroups = (a.sN + a.s_gl - 1) / a.s_gl;
+        a.n_groups = a.n_lgroups + 1;
+        warps = (long long)a.n_tiles * a.n_groups;
         const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
         const long long blocks = std::max(1LL, std::min(need, (long long)resident));
         // an ordinary launch: with a programmatic early start the persistent
