@@ -447,6 +447,26 @@ def _timer(stream):
     return avg
 
 
+def _oracle_ops(w, with_apply: bool):
+    """One FP64 oracle matvec (and block-Jacobi apply) of the workload on the host
+    cores, timed as it stands: the CPU baseline beside a report."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    J = oracle.Jacobian.from_workload(w)
+    x = np.random.default_rng(0).standard_normal(w.n)
+    t0 = time.perf_counter()
+    oracle.matvec(J, x)
+    out = {"matvec_ms": 1e3 * (time.perf_counter() - t0), "cores": oracle.max_threads(),
+           "kind": "oracle (dense blocks assembled on the fly)"}
+    if with_apply:
+        F = oracle.bj_setup(J)
+        t0 = time.perf_counter()
+        oracle.bj_apply(F, x)
+        out["apply_ms"] = 1e3 * (time.perf_counter() - t0)
+    return out
+
+
 def run_report(args):
     """Extra measurements beyond the default line (one JSON line each):
     nsweep  matvec time and handle memory vs N, factored vs dense, fitted exponents;
@@ -543,6 +563,8 @@ def run_report(args):
             torch.cuda.empty_cache()
         out["speedup"] = {k: out["dense"][k] / out["factored"][k] for k in ("matvec_ms", "apply_ms", "setup_ms",
                                                                              "gmres_ms")}
+        out["oracle"] = _oracle_ops(w, with_apply=False)
+        out["oracle"]["factored_matvec_speedup"] = out["oracle"]["matvec_ms"] / out["factored"]["matvec_ms"]
         print(json.dumps(out), flush=True)
         return
 
@@ -593,6 +615,7 @@ def run_report(args):
         f["apply_frac_hbm"] = f["apply_GBps"] / hbm_peak
         out["peaks"] = {"hbm_GBps": hbm_peak, "fp64_TFLOPs": fp64_peak, "source": src}
         out["speedup"] = {k: out["dense"][k] / f[k] for k in ("matvec_ms", "apply_ms", "setup_ms", "gmres_ms")}
+        out["oracle"] = _oracle_ops(w, with_apply=True)
         print(json.dumps(out), flush=True)
         return
 
