@@ -10,9 +10,14 @@
  *
  * and offers the Jacobian-vector product (Section 5.2), a block-Jacobi
  * preconditioner applied through the Sherman-Morrison-Woodbury formula
- * (Section 6, steps SMW-1..3), restarted right-preconditioned (F)GMRES
- * (Section 6, Eq. right_precond_system), the transposed operators and the
- * adjoint outer products used to differentiate x = J^-1 b.
+ * (Section 6, steps SMW-1..3), restarted right- or left-preconditioned (F)GMRES
+ * (Section 6, Eqs. right_precond_system / left_precond_system), the transposed
+ * operators and the adjoint outer products used to differentiate x = J^-1 b.
+ * Pair counts may differ from block to block (BR1-BSR pair_indptr, Section 5.1).
+ * A second handle type, sts_flow_t, generates the residual and the Jacobian of a
+ * toy HLL-flux flow model directly in this form (two rank-one pairs per face,
+ * Section 4.1) and runs an implicit Newton pseudo-time step around the solver
+ * (Section 3.3).
  *
  * Conventions shared by every call
  * --------------------------------
