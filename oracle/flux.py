@@ -31,6 +31,7 @@ Residual (Section 3.3, Eq. system_residual, unit cells and faces, outward normal
 from __future__ import annotations
 
 import dataclasses
+import functools
 
 import numpy as np
 
@@ -272,12 +273,18 @@ def residual(m: FluxModel, Lx: int, Ly: int, Q, Qn):
     return residual_rows(m, Lx, Ly, Q, Qn, range(Lx * Ly))[0]
 
 
-def _layout(m: FluxModel, Lx: int, Ly: int):
+@functools.lru_cache(maxsize=8)
+def _layout_of(N: int, w: int, Lx: int, Ly: int):
     from paper_2403_09198_gb300.inputs import diag_pattern, mesh_adjacency, off_pattern
     bptr, bidx = mesh_adjacency(Lx, Ly)
-    dp, di = diag_pattern(m.N, m.w)
-    op, oi = off_pattern(m.N)
+    dp, di = diag_pattern(N, w)
+    op, oi = off_pattern(N)
     return bptr, bidx, dp, di, op, oi
+
+
+def _layout(m: FluxModel, Lx: int, Ly: int):
+    """Block CSR of the grid and the two block patterns (shared, read-only arrays)."""
+    return _layout_of(m.N, m.w, Lx, Ly)
 
 
 def _grad_a_mag(m: FluxModel, q):
