@@ -382,8 +382,8 @@ def jacobian_blocks(m: FluxModel, Lx: int, Ly: int, Q):
                 c.append(a)
             pip.append(pip[-1] + row[2].shape[0])
     S, U, V, Sm, Um, Vm = (np.concatenate(c) for c in cols)
-    return dict(block_indptr=bptr, block_indices=bidx, d_indptr=dp, d_indices=di,
-                o_indptr=op, o_indices=oi, pair_indptr=np.asarray(pip, dtype=np.int32),
+    return dict(block_indptr=bptr.copy(), block_indices=bidx.copy(), d_indptr=dp.copy(), d_indices=di.copy(),
+                o_indptr=op.copy(), o_indices=oi.copy(), pair_indptr=np.asarray(pip, dtype=np.int32),
                 S=S, U=U, V=V, scales=dict(S=Sm, U=Um, V=Vm))
 
 
