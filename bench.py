@@ -661,6 +661,16 @@ def run_report(args):
             r["newton"] = {k: info[k] for k in ("iterations", "linear_iterations", "halvings", "res0", "res")}
             r["residual_history"] = hist.tolist()
             r["memory_GB"] = jac.memory_bytes() / 1e9
+            if not kw:
+                # inexact Newton: each linear solve to the Eisenstat-Walker forcing term
+                Qs = Qn.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info_f, hist_f = f.newton(jac, Qs, Qn, rtol=1e-10, forcing=True)
+                r["forcing"] = {"newton_step_ms": 1e3 * (time.perf_counter() - t0),
+                                "newton": {k: info_f[k] for k in ("iterations", "linear_iterations", "halvings",
+                                                                   "res0", "res")},
+                                "residual_history": hist_f.tolist()}
             out[name] = r
             jac.close()
             torch.cuda.empty_cache()

@@ -405,6 +405,12 @@ typedef struct {
     sts_gmres_opts gmres;     /* linear solves; vectors_on_host must be 0                */
     double *history;          /* optional HOST [max_newton + 1]: ||R|| before iteration 1,
                                  then after every iteration                              */
+    int forcing;              /* 0: every linear solve to gmres.rtol.  1: inexact Newton,
+                                 solve k to eta_k ||R_k|| (Eisenstat & Walker's choice 2,
+                                 gamma = 0.9, with the safeguards of Kelley 2003):
+                                 eta_0 = 0.9, eta_k = min(0.9, max(0.9 (r_k / r_{k-1})^2,
+                                 0.9 eta_{k-1}^2 if that exceeds 0.1,
+                                 0.5 tol / r_k)); gmres.rtol is then ignored             */
 } sts_newton_opts;
 
 typedef struct {

@@ -70,7 +70,8 @@ class sts_gmres_opts(ctypes.Structure):
 
 class sts_newton_opts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
-                ("max_halvings", ctypes.c_int), ("gmres", sts_gmres_opts), ("history", ctypes.c_void_p)]
+                ("max_halvings", ctypes.c_int), ("gmres", sts_gmres_opts), ("history", ctypes.c_void_p),
+                ("forcing", ctypes.c_int)]
 
 
 class sts_newton_info(ctypes.Structure):
@@ -429,7 +430,7 @@ class StsFlow:
 
     def newton(self, jac, Q, Qn, *, max_newton: int = 20, rtol: float = 1e-10, atol: float = 0.0,
                max_halvings: int = 8, gmres_rtol: float = 1e-10, restart: int = 30, gmres_max_iters: int = 1000,
-               precond: str = "bj", left: bool = False, raise_on_fail: bool = True):
+               precond: str = "bj", left: bool = False, forcing: bool = False, raise_on_fail: bool = True):
         """One pseudo-time step by Newton's method; Q (CUDA [n_cells, b]) is updated
         in place.  Returns (info dict, history of ||R||)."""
         self._states(Q, Qn)
@@ -438,6 +439,7 @@ class StsFlow:
         o.gmres.restart, o.gmres.max_iters, o.gmres.rtol = restart, gmres_max_iters, gmres_rtol
         o.gmres.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
         o.gmres.left = int(left)
+        o.forcing = int(forcing)
         hist = np.zeros(max_newton + 1)
         o.history = hist.ctypes.data
         info = sts_newton_info()

@@ -464,6 +464,9 @@ sts_status flow_newton(sts_flow_s *f, sts_jac_t jac, double *Q, const double *Qn
     }
     const double tol = std::max(rtol * r, atol);
     sts_status status = STS_OK;
+    // inexact Newton forcing (Eisenstat & Walker, choice 2; Kelley's safeguards)
+    constexpr double kEtaMax = 0.9, kGamma = 0.9;
+    double eta = kEtaMax, r_prev = r;
     while (true) {
         if (r <= tol) {
             inf.converged = 1;
@@ -481,7 +484,16 @@ sts_status flow_newton(sts_flow_s *f, sts_jac_t jac, double *Q, const double *Qn
         STS_TRY(sts_jac_update_values(jac, f->S, f->U, f->V, 0));
         if (d.gmres.precond != STS_PRECOND_NONE) STS_TRY(sts_jac_bjacobi_setup(jac));
         sts_gmres_info gi{};
-        const sts_status gs = sts_gmres_solve(jac, f->rhs, f->dQ, &d.gmres, &gi);
+        sts_gmres_opts go = d.gmres;
+        if (d.forcing) {
+            if (inf.iterations > 0) {
+                const double ea = kGamma * (r / r_prev) * (r / r_prev);
+                const double eb = kGamma * eta * eta > 0.1 ? std::max(ea, kGamma * eta * eta) : ea;
+                eta = std::min(kEtaMax, std::max(eb, 0.5 * tol / r));
+            }
+            go.rtol = eta;
+        }
+        const sts_status gs = sts_gmres_solve(jac, f->rhs, f->dQ, &go, &gi);
         if (gs != STS_OK && gs != STS_ERR_NOT_CONVERGED) return gs;
         inf.linear_iterations += gi.iterations;
         // line search: alpha = 1, 1/2, ... until ||R|| decreases
@@ -508,6 +520,7 @@ sts_status flow_newton(sts_flow_s *f, sts_jac_t jac, double *Q, const double *Qn
         }
         STS_CK(cudaMemcpyAsync(Q, f->Qt, n * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
         std::swap(f->R, f->Rt);
+        r_prev = r;
         r = rt;
         inf.res = r;
         if (d.history) d.history[inf.iterations] = r;

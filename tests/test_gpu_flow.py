@@ -164,3 +164,23 @@ def test_newton_rejects_a_foreign_handle():
     assert e.value.status == 1 and "layout" in e.value.message
     jac.close()
     f.close()
+
+
+def test_newton_inexact_forcing():
+    """Inexact Newton (Eisenstat-Walker forcing): the same root as the oracle's
+    Newton, in fewer GMRES iterations than solving every step to 1e-13."""
+    c = inputs.make_flow_case(6, 5, N=5, w=1, seed=12, dt=2.0)
+    m = flux.model_of(c)
+    Qo, _ = flux.newton(m, c.Lx, c.Ly, c.Qn, c.Qn, rtol=1e-13)
+    f = StsFlow(c)
+    jac = f.jacobian_handle()
+    runs = {}
+    for forcing in (False, True):
+        Q = dev(c.Qn.copy())
+        info, hist = f.newton(jac, Q, dev(c.Qn), rtol=1e-12, gmres_rtol=1e-13, forcing=forcing)
+        assert info["converged"] and info["res"] <= 1e-12 * info["res0"] and np.all(np.diff(hist) < 0)
+        assert np.linalg.norm(host(Q) - Qo) <= 1e-9 * np.linalg.norm(Qo)
+        runs[forcing] = info
+    assert runs[True]["linear_iterations"] < runs[False]["linear_iterations"]
+    jac.close()
+    f.close()
