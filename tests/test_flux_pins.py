@@ -157,6 +157,101 @@ def test_newton_converges_quadratically_to_a_root():
     assert r[k + 1] <= 10 * r[k] ** 2 or r[k + 1] <= 1e-13, r
 
 
+# ---------------------------------------------------------------- the Euler flux itself
+# conserved() and normal_flux() (Section 2.1 model, the f_n that Eq. HLL_flux wraps)
+# against forms written here from the textbook statement of the Euler equations,
+# not from the oracle: a calorically perfect gas in (rho, u, v, p), with the total
+# energy from gamma = (c_v + r) / c_v, and the exact rotational symmetry of the flux.
+
+
+def _model(N, r, cv, e0):
+    z = np.zeros(N)
+    return flux.FluxModel(N=N, w=0, r=np.asarray(r, float), cv=np.asarray(cv, float),
+                          e0=np.asarray(e0, float), beta=z, ws=z, K=np.zeros((N, 1)), A=0.0,
+                          theta=1.0, dt=1.0)
+
+
+def _euler_textbook(rho, u, v, p, n, gamma, rho_e0):
+    """Single-gas Euler state and normal flux from (rho, u, v, p): total energy
+    E = p / (gamma - 1) + rho e0 + rho |u|^2 / 2; F.n = (rho u_n, rho u u_n + p n_x,
+    rho v u_n + p n_y, (E + p) u_n)."""
+    E = p / (gamma - 1.0) + rho_e0 + 0.5 * rho * (u * u + v * v)
+    un = u * n[0] + v * n[1]
+    U = np.array([rho, rho * u, rho * v, E])
+    F = np.array([rho * un, rho * u * un + p * n[0], rho * v * un + p * n[1], (E + p) * un])
+    return U, F
+
+
+NORMALS = [(1.0, 0.0), (0.0, 1.0), (-1.0, 0.0), (0.6, -0.8), (-0.28, 0.96)]
+STATES = [(1.3, 0.4, -0.2, 0.9), (0.7, -1.1, 0.5, 2.2), (2.0, 0.0, 0.0, 1.0), (0.9, 2.7, 1.9, 0.6)]
+
+
+def _textbook_gap(nf, cons, N=1):
+    """Largest relative gap of (conserved, normal_flux) against the textbook Euler
+    state and flux over single-gas states (N = 1) or a mixture of N species with
+    one gas's constants (an effective single species of density sum rho_k)."""
+    r, cv, e0 = 0.287, 0.718, 0.05
+    m = _model(N, [r] * N, [cv] * N, [e0] * N)
+    gamma = (cv + r) / cv
+    frac = np.arange(1, N + 1, dtype=float)
+    frac /= frac.sum()
+    worst = 0.0
+    for rho, u, v, T in STATES:
+        q = np.concatenate([rho * frac, [u, v, T]])
+        p = rho * r * T
+        for n in NORMALS:
+            U, F = _euler_textbook(rho, u, v, p, n, gamma, rho * e0)
+            un = u * n[0] + v * n[1]
+            Ug = np.concatenate([rho * frac, U[1:]])
+            Fg = np.concatenate([rho * frac * un, F[1:]])
+            for got, ref in ((cons(m, q), Ug), (nf(m, q, n), Fg)):
+                worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    return worst
+
+
+@pytest.mark.parametrize("N", [1, 4])
+def test_euler_flux_matches_textbook_single_gas(N):
+    """N = 1, and N species that share one gas's constants (the mixture collapses
+    to one effective species): the oracle's conserved variables and normal flux
+    equal the textbook Euler ones to rounding, for normals along and off the axes."""
+    assert _textbook_gap(flux.normal_flux, flux.conserved, N) <= 1e-14
+
+
+def test_euler_flux_rotational_invariance():
+    """f(q, n) = R(n)^T f(R(n) q, e_x) for a mixture with distinct species constants:
+    rotating the velocity into the face frame, taking the x-direction flux and
+    rotating the momentum flux back gives the flux through the face."""
+    c, m = _case(N=5, w=1)
+    for q in c.Q[:6]:
+        N = m.N
+        for n in NORMALS:
+            u, v = q[N], q[N + 1]
+            qr = q.copy()
+            qr[N], qr[N + 1] = u * n[0] + v * n[1], -u * n[1] + v * n[0]
+            fr = flux.normal_flux(m, qr, (1.0, 0.0))
+            back = fr.copy()
+            back[N] = n[0] * fr[N] - n[1] * fr[N + 1]
+            back[N + 1] = n[1] * fr[N] + n[0] * fr[N + 1]
+            _close(flux.normal_flux(m, q, n), back, 1e-14)
+
+
+def test_mixture_flux_is_additive_over_identical_species():
+    """Splitting each species into two copies with the same constants and half
+    the density leaves the momentum and energy fluxes and the conserved momentum
+    and energy unchanged, and each species flux halves (Dalton's law and the
+    mass-weighted energy of Section 2.1)."""
+    c, m = _case(N=3, w=1)
+    m2 = _model(6, np.repeat(m.r, 2), np.repeat(m.cv, 2), np.repeat(m.e0, 2))
+    for q in c.Q[:4]:
+        N = m.N
+        q2 = np.concatenate([np.repeat(q[:N] / 2, 2), q[N:]])
+        for n in NORMALS[:3]:
+            f1, f2 = flux.normal_flux(m, q, n), flux.normal_flux(m2, q2, n)
+            _close(f2[2 * N:], f1[N:], 1e-14)
+            _close(f2[:2 * N].reshape(N, 2).sum(axis=1), f1[:N], 1e-14)
+        _close(flux.conserved(m2, q2)[2 * N:], flux.conserved(m, q)[N:], 1e-14)
+
+
 # ---------------------------------------------------------------- planted mistakes
 # Each plants one plausible mistake in the oracle (on the CPU, through monkeypatch)
 # and checks that the pin it should trip reports it: the pins above are not
@@ -232,3 +327,30 @@ def test_planted_assembly_mistake_is_caught(monkeypatch):
     Jcs = _cs_jacobian(lambda x: flux.residual(m, c.Lx, c.Ly, x.reshape(c.n_cells, m.b), c.Qn).ravel(),
                        c.Q.ravel())
     assert np.abs(D - Jcs).max() > 1e-6 * np.abs(Jcs).max()
+
+
+def test_planted_pressure_term_mistake_is_caught(monkeypatch):
+    """An x-momentum flux without its pressure term p n_x fails the textbook pin."""
+    real = flux.normal_flux
+
+    def wrong(m_, q, n):
+        f = real(m_, q, n)
+        T = q[m_.N + 2]
+        f[m_.N] -= (q[:m_.N] * m_.r).sum() * T * n[0]
+        return f
+    assert _textbook_gap(real, flux.conserved) <= 1e-14
+    monkeypatch.setattr(flux, "normal_flux", wrong)
+    assert _textbook_gap(flux.normal_flux, flux.conserved) > 1e-3
+
+
+def test_planted_energy_mistake_is_caught(monkeypatch):
+    """A total energy without the kinetic part fails the textbook pin."""
+    real = flux.conserved
+
+    def wrong(m_, q):
+        U = real(m_, q)
+        N = m_.N
+        U[N + 2] -= 0.5 * q[:N].sum() * (q[N] ** 2 + q[N + 1] ** 2)
+        return U
+    monkeypatch.setattr(flux, "conserved", wrong)
+    assert _textbook_gap(flux.normal_flux, flux.conserved) > 1e-3
