@@ -398,10 +398,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": dict(_config(w), ops_per_step={"matvec_fp64": counted["mv"], "bj_apply_fp64": counted["ap"],
-                                                 "explicit_loops": ops},
-                       parallelism="replicas" if ws > 1 else "single GPU",
-                       vec_layout="component-major"),
+        "config": _config(w),
+        "run": {"ops_per_step": {"matvec_fp64": counted["mv"], "bj_apply_fp64": counted["ap"],
+                                 "explicit_loops": ops},
+                "parallelism": "replicas" if ws > 1 else "single GPU", "vec_layout": "component-major"},
         "roofline": {"bound": "alu", "kernel": "sts_jac_matvec FP64 (k_dots + k_mv_struct)",
                      "achieved": ach_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": ach_tflops / fp64_peak,

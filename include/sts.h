@@ -209,9 +209,10 @@ sts_status sts_jac_matvec(sts_jac_t h, const double *x, double *y, int trans);
  * doubles of scratch, at most 2^19 (for example 16384 cells with 21 dot tasks,
  * the 128x128, N = 60 workload, use 344064); larger handles get
  * STS_ERR_INVALID_ARG and should use sts_jac_matvec.
- * The first call made on a device (with that device current) looks up the
- * buffer's address with cudaGetSymbolAddress; make that first call before
- * any stream capture.  All calls share the one buffer: calls that overlap on
+ * The handle's device (the one current at sts_jac_create) must be the current
+ * device during the call, else STS_ERR_INVALID_ARG.  The first call for a
+ * handle of a given device looks up that device's buffer address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  All calls share the one buffer: calls that overlap on
  * the GPU (different streams or threads) race on it and must be serialised by
  * the caller.  Factored representation only; trans = 1 needs enable_transpose.
  * The paper has no counterpart to this entry point.  Asynchronous.

@@ -17,25 +17,36 @@ class ImplicitSolve(torch.autograd.Function):
     """``x = ImplicitSolve.apply(b, S, U, V, jac, rtol, restart)``.
 
     ``jac`` is a :class:`StsJacobian` created with ``transpose=True`` on the same
-    structure; its values are replaced by (S, U, V) in the forward pass.
+    structure; its values are replaced by (S, U, V) in the forward pass.  One
+    handle may serve several solves of one graph (for example unrolled
+    pseudo-time steps): the backward pass reloads this solve's (S, U, V) and
+    sets the preconditioner up again when the handle's values have changed
+    since its forward pass.
     """
 
     @staticmethod
     def forward(ctx, b, S, U, V, jac: StsJacobian, rtol: float = 1e-10, restart: int = 30):
-        jac.update_values(S.detach(), U.detach(), V.detach())
+        S, U, V = S.detach(), U.detach(), V.detach()
+        jac.update_values(S, U, V)
         jac.bjacobi_setup()
         x, info = jac.gmres(b.detach(), rtol=rtol, restart=restart)
         ctx.jac = jac
         ctx.rtol = rtol
         ctx.restart = restart
-        ctx.save_for_backward(x)
+        ctx.version = jac.values_version
+        ctx.save_for_backward(x, S, U, V)
         ctx.info = info
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        (x,) = ctx.saved_tensors
+        x, S, U, V = ctx.saved_tensors
         jac: StsJacobian = ctx.jac
+        if jac.values_version != ctx.version:
+            # another solve (or a Newton step) has loaded other values since
+            jac.update_values(S, U, V)
+            jac.bjacobi_setup()
+            ctx.version = jac.values_version
         lam, _ = jac.gmres(gx.contiguous(), rtol=ctx.rtol, restart=ctx.restart, trans=True)
         gS, gU, gV = jac.grad(lam, x)
         return lam, gS, gU, gV, None, None, None

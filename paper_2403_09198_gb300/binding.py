@@ -224,6 +224,8 @@ class StsJacobian:
         h = ctypes.c_void_p()
         check(self.lib.sts_jac_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h
+        # bumped whenever the handle's values change (update_values, a Newton step)
+        self.values_version = 0
         self.mixed = mixed
         self.n = self.n_cells * self.b
         # sizes of the public value arrays (index bookkeeping only)
@@ -252,6 +254,7 @@ class StsJacobian:
         on_host = isinstance(S, np.ndarray)
         if on_host:
             S, U, V = (np.ascontiguousarray(a, dtype=np.float64) for a in (S, U, V))
+        self.values_version += 1
         check(self.lib.sts_jac_update_values(self.h, _ptr(S), _ptr(U), _ptr(V), int(on_host)))
         if on_host:
             self.stream.synchronize()   # host arrays must outlive the copies
@@ -443,6 +446,7 @@ class StsFlow:
         hist = np.zeros(max_newton + 1)
         o.history = hist.ctypes.data
         info = sts_newton_info()
+        jac.values_version += 1          # the step writes its own Jacobians into jac
         st = self.lib.sts_flow_newton(self.h, jac.h, _ptr(Q), _ptr(Qn), ctypes.byref(o), ctypes.byref(info))
         if raise_on_fail:
             check(st)

@@ -40,6 +40,17 @@ sts_status dev_alloc(sts_jac_s *h, void **p, size_t bytes) {
     return STS_OK;
 }
 
+void dev_free(sts_jac_s *h, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i].p == p) {
+            cudaFree(p);
+            h->bytes -= h->allocs[i].bytes;
+            h->allocs.erase(h->allocs.begin() + (long)i);
+            return;
+        }
+}
+
 // Band half-width w if rows p < N = b - kStructNF hold exactly the level band
 // |p - q| <= w followed by the kStructNF flow columns and the last kStructNF
 // rows are dense; -1 if the pattern is not of that family.
@@ -509,6 +520,7 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
             delete h;
             return set_error(STS_ERR_CUDA, "sts_jac_create: cannot query the device");
         }
+        h->device = dev;
     }
     h->bptr.assign(d->block_indptr, d->block_indptr + nc + 1);
     h->bidx.assign(d->block_indices, d->block_indices + nnzb);

@@ -330,10 +330,19 @@ sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
     Krylov &K = h->kry;
     const size_t n = (size_t)h->b * h->ncp;
     if (K.m < m) {
-        // the old buffers stay owned by the handle (freed at destroy); only grow
+        // a larger restart replaces the basis buffers (the stream is idle here:
+        // every solve ends with a synchronisation)
+        STS_CK(cudaStreamSynchronize(h->stream));
+        dev_free(h, K.V);
+        dev_free(h, K.Z);
+        dev_free(h, K.Z32);
+        dev_free(h, K.partial);
+        dev_free(h, K.red);
+        K.V = K.Z = K.partial = K.red = nullptr;
+        K.Z32 = nullptr;
+        K.m = 0;
         STS_TRY(dalloc(h, &K.V, (size_t)(m + 1) * n));
         STS_TRY(dalloc(h, &K.Z, (size_t)m * n));
-        K.Z32 = nullptr;
         STS_TRY(dalloc(h, &K.partial, (size_t)kRedBlocks * (m + 2)));
         STS_TRY(dalloc(h, &K.red, (size_t)3 * (m + 2)));
         if (!K.ticket) {

@@ -604,13 +604,19 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &args) {
             case 3: kern = mv_struct_kernel<T, 3>(nreg); break;
             default: kern = mv_struct_kernel<T, 4>(nreg); break;
         }
-        int &resident = h->mvs_blocks[sizeof(T) == 8 ? 0 : 1];    // blocks resident at once, found once
+        // blocks resident at once, found once per kernel instance and shared-memory
+        // size: the instance (pair slots) and the row length differ between the
+        // forward and transposed plans
+        int resident = 0;
+        for (const auto &e : h->mvs_resident)
+            if (e.kern == reinterpret_cast<const void *>(kern) && e.smem == smem) resident = e.blocks;
         if (!resident) {
             if (smem > 48 * 1024)
                 STS_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int per_sm = 0;
             STS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * kTile, smem));
             resident = std::max(per_sm, 1) * h->nsm;
+            h->mvs_resident.push_back({reinterpret_cast<const void *>(kern), smem, resident});
         }
         a.s_gl = pass2_group_rows(a.sN, a.n_tiles, (long long)resident * kWarpsPerBlock, a.s_gl);
         a.n_lgroups = (a.sN + a.s_gl - 1) / a.s_gl;
@@ -667,8 +673,8 @@ sts_status mv_dots64(sts_jac_s *h, int dir, const double *x, double *c) {
 // library-owned, file-scope device array instead of a handle buffer.  The
 // array (kNoAllocScratch doubles, 4 MiB) exists on every GPU that loads the
 // library, for the life of the process.  Its device address is looked up with
-// cudaGetSymbolAddress once per device, on the first call made while that
-// device is current.  Every call shares the array, so calls that overlap on the
+// cudaGetSymbolAddress once per device, on the first call for a handle of that
+// device (which must be the current device during the call).  Every call shares the array, so calls that overlap on the
 // GPU (several streams, several threads) race on it; each call writes every
 // entry it later reads, so nothing has to be cleared between calls.
 constexpr size_t kNoAllocScratch = size_t(1) << 19;
@@ -688,8 +694,13 @@ sts_status mv_apply64_noalloc(sts_jac_s *h, int dir, const double *x, double *y)
                          "sts_jac_matvec_noalloc: this Jacobian needs %zu scratch values (tiles x dot tasks x 32), "
                          "more than the %zu of the static buffer; use sts_jac_matvec",
                          need, kNoAllocScratch);
-    int dev = 0;
-    STS_CK(cudaGetDevice(&dev));
+    // the scratch address belongs to the handle's device, which must be current
+    const int dev = h->device;
+    int cur = -1;
+    STS_CK(cudaGetDevice(&cur));
+    if (cur != dev)
+        return set_error(STS_ERR_INVALID_ARG,
+                         "sts_jac_matvec_noalloc: the handle lives on device %d but device %d is current", dev, cur);
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return set_error(STS_ERR_INVALID_ARG, "sts_jac_matvec_noalloc: device %d out of range", dev);
     double *c = nullptr;
@@ -724,7 +735,6 @@ static sts_status to_internal(sts_jac_s *h, const T *x, T *xi) {
         k_comp_pad<T><<<grid_for(n, 256), 256, 0, h->stream>>>(x, xi, h->nc, h->b, h->ncp);
         STS_LAUNCHED();
     }
-    STS_LAUNCHED();
     return STS_OK;
 }
 
@@ -739,7 +749,6 @@ static sts_status from_internal(sts_jac_s *h, const T *xi, T *x) {
         k_comp_unpad<T><<<grid_for(n, 256), 256, 0, h->stream>>>(xi, x, h->nc, h->b, h->ncp);
         STS_LAUNCHED();
     }
-    STS_LAUNCHED();
     return STS_OK;
 }
 

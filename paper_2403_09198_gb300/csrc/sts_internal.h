@@ -258,8 +258,14 @@ struct sts_jac_s {
     // before its grid-dependency wait.
     bool streams_dirty = true;
     // launch data computed on first use (per precision: 0 FP64, 1 FP32)
+    int device = 0;                     // CUDA device current at creation
     int nsm = 0;                        // SMs of the handle's device
-    int mvs_blocks[2] = {0, 0};         // grid of the structured pass 2
+    struct Resident {                   // resident blocks of one structured pass-2 instance
+        const void *kern;
+        size_t smem;
+        int blocks;
+    };
+    std::vector<Resident> mvs_resident;
     bool sap_attr[2] = {false, false};  // shared-memory limit of the structured apply set
     // host copies of the structure
     std::vector<int> bptr, bidx, dptr, didx, optr, oidx;
@@ -289,8 +295,9 @@ namespace sts {
 // Band half-width of a pattern of the structured family, or -1 (api.cu).
 int struct_band(int b, const std::vector<int> &ptr, const std::vector<int> &idx);
 
-// allocation helpers (api.cu)
+// allocation helpers (api.cu); dev_free releases one tracked allocation
 sts_status dev_alloc(sts_jac_s *h, void **p, size_t bytes);
+void dev_free(sts_jac_s *h, void *p);
 template <typename T>
 inline sts_status dalloc(sts_jac_s *h, T **p, size_t n) {
     return dev_alloc(h, reinterpret_cast<void **>(p), n * sizeof(T));

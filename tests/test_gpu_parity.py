@@ -402,6 +402,32 @@ def test_implicit_solve_autograd_vs_oracle_and_fd():
     jac.close()
 
 
+def test_implicit_solve_two_solves_share_one_handle():
+    """Two ImplicitSolve calls with different values on one handle in one graph
+    (as in unrolled pseudo-time steps): each solve's gradients equal the oracle
+    adjoint of its own Jacobian, although the handle holds the second solve's
+    values when the first one's backward runs."""
+    import torch
+    from paper_2403_09198_gb300.autograd import ImplicitSolve
+    w = inputs.make_workload(4, 3, N=3, w=1, r_diag=2, r_off=1, seed=23, dt=0.2)
+    S2, U2, V2 = 1.1 * w.S, 0.9 * w.U, 1.2 * w.V
+    J1, J2 = oracle_jac(w), oracle_jac(w, S=S2, U=U2, V=V2)
+    rhs2 = np.random.default_rng(24).standard_normal(w.n)
+    jac = _jac(w, transpose=True)
+    Wd = dev(w.W)
+    p1 = [dev(a).requires_grad_(True) for a in (w.rhs, w.S, w.U, w.V)]
+    p2 = [dev(a).requires_grad_(True) for a in (rhs2, S2, U2, V2)]
+    x1 = ImplicitSolve.apply(*p1, jac, 1e-14, 30)
+    x2 = ImplicitSolve.apply(*p2, jac, 1e-14, 30)
+    L = 0.5 * torch.sum((Wd * x1) ** 2) + 0.5 * torch.sum((Wd * x2) ** 2)
+    L.backward()
+    for params, J, rhs in ((p1, J1, w.rhs), (p2, J2, rhs2)):
+        ref = oracle.adjoint(J, rhs, w.W)
+        for p, r in zip(params, (ref["gb"], ref["gS"], ref["gU"], ref["gV"])):
+            assert rel_err(host(p.grad), r) <= 1e-10
+    jac.close()
+
+
 def test_adjoint_full_size_sampled():
     """128 x 128, N = 60, seed 4: adjoint GMRES on the transposed operators; the
     oracle checks J^T lambda = W^2 x on sampled rows and the outer products."""
