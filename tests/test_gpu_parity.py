@@ -313,6 +313,23 @@ def test_gmres_full_size_true_residual():
     jac.close()
 
 
+def test_gmres_full_size_solution_parity():
+    """128 x 128, N = 60: both solvers run to rtol 1e-14, where the solution is
+    determined to about kappa 1e-14; the GPU and oracle solutions then agree to
+    1e-12 (reading (iv) of GMRES parity)."""
+    w = full("grid128_N60")
+    J = oracle_jac(w)
+    jac = _jac(w)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), restart=30, rtol=1e-14)
+    assert info.converged
+    xo, io = oracle.gmres(J, w.rhs, restart=30, rtol=1e-14)
+    assert io["true_rel"] <= 1e-14
+    assert sol_err(host(x), xo) <= TOL64
+    assert abs(info.iterations - io["iterations"]) <= 1
+    jac.close()
+
+
 # ---------------------------------------------------------------- mixed precision
 
 
@@ -346,6 +363,39 @@ def test_mixed_precision_fgmres(dt):
     assert np.linalg.norm(z32 - zo) / np.linalg.norm(zo) <= 1e-6
     del torch
     jac.close()
+
+
+def test_mixed_precision_full_size_weak_diagonal():
+    """512 x 512 cells, N = 60 (the mixed-precision workload's mesh and levels,
+    seed 3) with dt = 1 instead of 1e-3, so that J is far from a scaled identity:
+    FP32 matvec and block-Jacobi inside FP64 flexible GMRES reach a true FP64
+    residual of 1e-10 (recomputed by the oracle), and the solution differs from
+    the oracle's FP64 GMRES solution (rtol 1e-12) by at most kappa * 1e-10.
+    kappa is estimated from below by the oracle alone: sigma_max by power
+    iterations on J^T J, 1 / sigma_min by ||x|| / ||b||; a smaller estimate only
+    tightens the bound."""
+    w = inputs.make_workload(512, 512, N=60, w=2, r_diag=2, r_off=1, seed=3, dt=1.0)
+    J = oracle_jac(w)
+    jac = _jac(w, mixed=True)
+    jac.bjacobi_setup()
+    x, info = jac.gmres(dev(w.rhs), rtol=1e-10, restart=30, mixed=True)
+    xm = host(x)
+    jac.close()
+    assert info.converged
+    bn = np.linalg.norm(w.rhs)
+    assert np.linalg.norm(w.rhs - oracle.matvec(J, xm)) <= 1e-10 * bn * (1 + 1e-6)
+    xo, io = oracle.gmres(J, w.rhs, restart=30, rtol=1e-12)
+    assert io["true_rel"] <= 1e-12
+    rng = np.random.default_rng(31)
+    v = rng.standard_normal(w.n)
+    for _ in range(6):
+        v = oracle.matvec(J, oracle.matvec(J, v), trans=True)
+        v /= np.linalg.norm(v)
+    smax = np.sqrt(np.linalg.norm(oracle.matvec(J, oracle.matvec(J, v), trans=True)))
+    kappa = smax * np.linalg.norm(xo) / bn
+    assert kappa > 2.0, kappa          # the bound is not vacuous
+    err = np.linalg.norm(xm - xo) / np.linalg.norm(xo)
+    assert err <= kappa * (1e-10 + 1e-12), (err, kappa)
 
 
 # ---------------------------------------------------------------- adjoint
@@ -450,6 +500,63 @@ def test_adjoint_full_size_sampled():
     rS, rU, rV = oracle.grad(J, lh, xh)
     for a, b in ((gS, rS), (gU, rU), (gV, rV)):
         assert rel_err(host(a), b) <= TOL64
+    jac.close()
+
+
+def test_adjoint_full_size_fd_and_oracle_gradient():
+    """128 x 128, N = 60, seed 4 (the adjoint workload): ImplicitSolve's
+    gradients with respect to b, S, U and V equal the oracle's adjoint gradient
+    element by element, and 64 central finite differences (16 per parameter
+    group) agree with g . d to 1e-6 relative.  Directions have N(0, 1) entries
+    and the step is h = 1e-3 per entry: a solve determines L only to about
+    eps L, so a central difference carries an error near eps L / h, which at
+    h = 1e-6 is 1e-5 of the directional derivatives here (about 1e-5); at
+    h = 1e-3 it is 1e-8 of them, while J moves by about 1e-6 of its diagonal,
+    so the O(h^2) truncation stays near 1e-9 relative.  L(p + h d) - L(p - h d)
+    is formed as 0.5 sum W^2 (x+ - x-)(x+ + x-).  Each solve runs a fixed
+    number of Arnoldi steps (that of the base solve to rtol 1e-14, plus two),
+    so the computed solution is a smooth function of the data."""
+    import torch
+    from paper_2403_09198_gb300.autograd import ImplicitSolve
+    w = full("grid128_N60_adjoint")
+    jac = _jac(w, transpose=True)
+    Wd = dev(w.W)
+    params = [dev(a).requires_grad_(True) for a in (w.rhs, w.S, w.U, w.V)]
+    x = ImplicitSolve.apply(*params, jac, 1e-14, 30)
+    L = 0.5 * torch.sum((Wd * x) ** 2)
+    L.backward()
+    grads = [p.grad.detach().clone() for p in params]
+    J = oracle_jac(w)
+    ref = oracle.adjoint(J, w.rhs, w.W)
+    for g, r in zip(grads, (ref["gb"], ref["gS"], ref["gU"], ref["gV"])):
+        assert rel_err(host(g), r) <= 1e-10
+    base = [p.detach() for p in params]
+    jac.update_values(base[1], base[2], base[3])
+    jac.bjacobi_setup()
+    _, info0 = jac.gmres(base[0], rtol=1e-14)
+    steps = min(info0.iterations + 2, 30)
+
+    def solve(ps):
+        jac.update_values(ps[1], ps[2], ps[3])
+        jac.bjacobi_setup()
+        xs, _ = jac.gmres(ps[0], rtol=1e-300, restart=30, max_iters=steps, raise_on_fail=False)
+        return xs
+
+    gnorm = float(torch.sqrt(sum(torch.sum(g * g) for g in grads)))
+    gen = torch.Generator(device="cuda").manual_seed(41)
+    h = 1e-3
+    W2 = Wd * Wd
+    for k in range(64):
+        grp = k % 4
+        d = torch.randn(base[grp].shape, generator=gen, device="cuda", dtype=torch.float64)
+        gd = float(torch.sum(grads[grp] * d))
+        pp, pm = list(base), list(base)
+        pp[grp] = base[grp] + h * d
+        pm[grp] = base[grp] - h * d
+        xp = solve(pp)
+        xm = solve(pm)
+        fd = float(0.5 * torch.sum(W2 * (xp - xm) * (xp + xm))) / (2 * h)
+        assert abs(gd - fd) <= 1e-6 * max(abs(fd), 1e-12 * gnorm), (k, grp, gd, fd)
     jac.close()
 
 
