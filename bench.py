@@ -477,7 +477,10 @@ def run_report(args):
     newton  128x128, N=60 HLL-flux model: residual, Jacobian generation, values update,
             setup, GMRES, and one Newton pseudo-time step, factored vs dense;
     kernels 128x128, N=60: three rounds of FP64 and FP32 matvec and apply, a short
-            fixed launch sequence for kernel profilers (no timing)."""
+            fixed launch sequence for kernel profilers (no timing);
+    dd      128x128, N=60 cut into 1, 2 (strips) and 4 (2 x 2 tiles) parts held by this
+            process: matvec with its halo exchange, block-Jacobi, GMRES to 1e-10,
+            against the single handle."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -488,6 +491,56 @@ def run_report(args):
     stream = torch.cuda.current_stream()
     avg = _timer(stream)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    if args.report == "dd":
+        from paper_2403_09198_gb300.dd import DdPlan, DdSolver, grid_partition
+        w = inputs.named_workload("grid128_N60")
+        S, U, V = t(w.S), t(w.U), t(w.V)
+        ref = StsJacobian(w, S, U, V, layout="component")
+        ref.bjacobi_setup()
+        xv = torch.randn(w.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(xv)
+        b = t(w.rhs.reshape(w.n_cells, w.b).T.ravel())
+        out = {"report": "dd", "workload": "grid128_N60: 128x128 cells, N=60, b=63, 2/1 pairs",
+               "single": {"matvec_ms": avg(lambda: ref.matvec(xv, out=y), 50),
+                          "apply_ms": avg(lambda: ref.bjacobi_apply(xv, out=y), 50)}}
+        ref.gmres(b, rtol=1e-10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = ref.gmres(b, rtol=1e-10)
+        out["single"].update(gmres_ms=1e3 * (time.perf_counter() - t0), iterations=info.iterations)
+        for name, (px, py) in (("1 part", (1, 1)), ("2 strips", (1, 2)), ("2x2 tiles", (2, 2))):
+            part = grid_partition(128, 128, px, py)
+            plans, jacs = [], []
+            for p in range(px * py):
+                P = DdPlan(w.block_indptr, w.block_indices, part, px * py, p)
+                L, (Sl, Ul, Vl) = P.gather(w, S, U, V)
+                j = StsJacobian(L, Sl, Ul, Vl, layout="component")
+                j.bjacobi_setup()
+                plans.append(P)
+                jacs.append(j)
+            solver = DdSolver(jacs, plans)
+            xs = [torch.randn(P.n_local * w.b, dtype=torch.float64, device="cuda") for P in plans]
+            bs = []
+            for P in plans:
+                loc = w.rhs.reshape(w.n_cells, w.b)[P.local_to_global]
+                bs.append(t(np.ascontiguousarray(loc.T).ravel()))
+            r = {"parts": px * py, "ghost_cells": int(sum(P.n_ghost for P in plans)),
+                 "matvec_ms": avg(lambda: solver.matvec(xs), 50),
+                 "apply_ms": avg(lambda: solver.bjacobi_apply(xs), 50)}
+            solver.gmres(bs, rtol=1e-10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = solver.gmres(bs, rtol=1e-10)
+            r.update(gmres_ms=1e3 * (time.perf_counter() - t0), iterations=info.iterations,
+                     true_rel_residual=info.true_rel_residual)
+            out[name] = r
+            solver.close()
+            for j in jacs:
+                j.close()
+        ref.close()
+        print(json.dumps(out), flush=True)
+        return
 
     if args.report == "kernels":
         w = inputs.named_workload("grid128_N60")
@@ -744,7 +797,7 @@ def main():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels", "pairs", "newton"], default=None,
+    p.add_argument("--report", choices=["nsweep", "large", "mixed", "kernels", "pairs", "newton", "dd"], default=None,
                    help="print an extra measurement instead of the benchmark line")
     args = p.parse_args()
     if args.report:

@@ -62,7 +62,8 @@ enum {
     STS_ERR_NOT_CONVERGED = 5, /* GMRES hit max_iters; the returned x is still valid    */
     STS_ERR_NUMERIC = 6,       /* NaN or Inf met in a residual or Krylov quantity       */
     STS_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up (see bjacobi_apply) */
-    STS_ERR_NOT_SETUP = 8      /* block-Jacobi used before sts_jac_bjacobi_setup        */
+    STS_ERR_NOT_SETUP = 8,     /* block-Jacobi used before sts_jac_bjacobi_setup        */
+    STS_ERR_COMM = 9           /* a communication or operation callback reported failure */
 };
 
 enum { STS_F64 = 0, STS_MIXED = 2 };                       /* sts_jac_desc.dtype        */
@@ -303,6 +304,202 @@ sts_status sts_selftest_bounded_wait(void *stream);
 
 /* Destroy a handle and free its device memory.  NULL is accepted. */
 sts_status sts_jac_destroy(sts_jac_t h);
+
+/* ---------------------------------------------------------------------------
+ * Domain decomposition (spatial partition of the cells over several parts,
+ * one sub-domain handle per part).
+ *
+ * The block adjacency of Section 5.1 couples a cell only with its face
+ * neighbours, and the block-Jacobi preconditioner of Section 6 is one block per
+ * cell, so the hot path shards by cells: a part owns the block rows of its
+ * cells, the matvec needs the vector at a halo of neighbouring cells ("ghost"
+ * cells, owned by other parts) and the preconditioner needs nothing from other
+ * parts.  GMRES then needs sums over all parts for its dot products.
+ *
+ * Part p's sub-domain is an ordinary square sts_jac_t over its local cells:
+ * the owned cells (ascending global id) followed by the ghost cells (ascending
+ * global id), ghosts being the cells of other parts that share a block with an
+ * owned cell in either direction.  An owned row keeps all its blocks; a ghost
+ * row keeps its diagonal block and its blocks into owned columns.  Once the
+ * ghost entries of x hold the neighbours' values, the local product gives the
+ * exact rows of J x at owned cells, and the local transposed product the exact
+ * rows of J^T x at owned cells; the values at ghost rows are not used.
+ */
+typedef struct sts_dd_plan_s *sts_dd_plan_t;
+
+/*
+ * Build part `part`'s sub-domain plan from the global block CSR (HOST int32,
+ * the sts_jac_desc arrays) and a partition part_of_cell[n_cells] with values
+ * in [0, n_parts).  Every part computes its own plan; the plans of two
+ * neighbouring parts agree on the order of the cells they exchange (ascending
+ * global id).  Errors: STS_ERR_INVALID_ARG (bad CSR or partition, a part with
+ * no cell).  Host only; no GPU is used.
+ */
+sts_status sts_dd_plan_create(int n_cells, const int *block_indptr, const int *block_indices, int n_parts,
+                              const int *part_of_cell, int part, sts_dd_plan_t *out);
+
+typedef struct {
+    int n_owned, n_ghost, n_local;   /* n_local = n_owned + n_ghost                          */
+    int nnzb;                        /* blocks of the local block CSR                        */
+    int n_neighbors;                 /* parts this part exchanges with                       */
+    int n_send, n_recv;              /* cells sent / received over all neighbours            */
+} sts_dd_sizes;
+
+sts_status sts_dd_plan_sizes(sts_dd_plan_t plan, sts_dd_sizes *sizes);
+
+/*
+ * Copy the plan into HOST int32 arrays sized by sts_dd_plan_sizes:
+ *   local_to_global[n_local]       global cell of every local cell
+ *   block_indptr[n_local+1], block_indices[nnzb]   local block CSR (local cell ids,
+ *                                  rows ascending), ready for sts_jac_desc
+ *   block_map[nnzb]                global block id (position in the global
+ *                                  block_indices) of every local block
+ *   neighbors[n_neighbors]         neighbour part ids, ascending
+ *   send_ptr[n_neighbors+1], send_cells[n_send]   owned local cells sent to neighbour k:
+ *                                  send_cells[send_ptr[k] .. send_ptr[k+1])
+ *   recv_ptr[n_neighbors+1], recv_cells[n_recv]   ghost local cells received from
+ *                                  neighbour k, in the order neighbour k sends them
+ * Any pointer may be NULL to skip that array.
+ */
+sts_status sts_dd_plan_get(sts_dd_plan_t plan, int *local_to_global, int *block_indptr, int *block_indices,
+                           int *block_map, int *neighbors, int *send_ptr, int *send_cells, int *recv_ptr,
+                           int *recv_cells);
+
+/*
+ * Sizes of the local value arrays for the global layout given (pair_indptr,
+ * the global BR1-BSR pair_indptr[nnzb+1] HOST, or NULL with uniform r_diag /
+ * r_off): *nnz_S values of S and *n_pairs pairs, and the local pair_indptr
+ * (HOST [nnzb_local+1]; may be NULL).
+ */
+sts_status sts_dd_plan_value_sizes(sts_dd_plan_t plan, int nnz_d, int nnz_o, const int *pair_indptr, int r_diag,
+                                   int r_off, long long *nnz_S, int *n_pairs, int *local_pair_indptr);
+
+/*
+ * Gather the local values (the blocks listed in block_map, in local order, and
+ * their pairs) from the global S, U, V of the public layout.  on_host = 0:
+ * device pointers, one gather kernel on `stream` (asynchronous); on_host = 1:
+ * host pointers, copied on the host (synchronous).  The local arrays are sized
+ * by sts_dd_plan_value_sizes (U, V: [n_pairs][block_size]).
+ */
+sts_status sts_dd_plan_gather(sts_dd_plan_t plan, int block_size, int nnz_d, int nnz_o, const int *pair_indptr,
+                              int r_diag, int r_off, const double *S, const double *U, const double *V,
+                              double *S_local, double *U_local, double *V_local, int on_host, void *stream);
+
+sts_status sts_dd_plan_destroy(sts_dd_plan_t plan);
+
+/*
+ * Communication with the parts held by other processes, supplied by the
+ * caller (for instance torch.distributed over NCCL).  Both callbacks return 0
+ * on success; any other value makes the calling library function return
+ * STS_ERR_COMM.
+ *   exchange: send n_send messages and receive n_recv messages at once;
+ *             send message k goes from part send_from[k] (held here) to part
+ *             send_to[k], receive message k from part recv_from[k] to part
+ *             recv_to[k] (held here); a (from, to) pair names one message.  A
+ *             message holds send_len[k] (recv_len[k]) doubles: the b values of
+ *             each listed cell, cell after cell, in the plans' order.  Buffers are
+ *             device memory written (read) by work on `stream`: the callback
+ *             must order its transfers after the work already queued on
+ *             `stream`, and the work queued afterwards after its receives.
+ *   allreduce: replace vals[0 .. count) (HOST memory) by their sums over all
+ *             processes; every process calls it with the same count.
+ */
+typedef struct {
+    void *ctx;
+    int (*exchange)(void *ctx, int n_send, const int *send_from, const int *send_to, const double *const *send_buf,
+                    const int *send_len, int n_recv, const int *recv_from, const int *recv_to,
+                    double *const *recv_buf, const int *recv_len, void *stream);
+    int (*allreduce)(void *ctx, double *vals, int count);
+} sts_dd_comm;
+
+typedef struct sts_dd_s *sts_dd_t;
+
+/*
+ *   n_parts              parts held by this process (>= 1)
+ *   part_ids[n_parts]    their ids in the partition
+ *   jac[n_parts]         sub-domain handles created from the plans' local layouts
+ *                        (sts_dd_plan_get, sts_dd_plan_gather), factored
+ *                        representation, one stream shared by all of them
+ *   plans[n_parts]       the plans of those parts (kept by the caller until destroy)
+ *   comm                 NULL when every part of the partition is in this process;
+ *                        otherwise the callbacks above
+ */
+typedef struct {
+    int n_parts;
+    const int *part_ids;
+    sts_jac_t *jac;
+    sts_dd_plan_t *plans;
+    const sts_dd_comm *comm;
+} sts_dd_desc;
+
+/* Check the parts and upload the exchange lists.  Synchronous. */
+sts_status sts_dd_create(const sts_dd_desc *desc, sts_dd_t *out);
+
+/*
+ * y = J x (trans = 0) or J^T x (trans = 1) over the whole partition.  x[k],
+ * y[k]: device vectors of local part k (n_local * b entries, the handle's
+ * layout).  The ghost entries of x are ignored (their values come from the
+ * neighbours, by one halo exchange); the ghost entries of y are set to zero.
+ * Asynchronous on the parts' stream.
+ */
+sts_status sts_dd_matvec(sts_dd_t dd, const double *const *x, double *const *y, int trans);
+
+/* z = M x per part (Section 6, block-Jacobi through SMW; no communication);
+ * needs sts_jac_bjacobi_setup on every part.  Ghost entries of z are set to zero. */
+sts_status sts_dd_bjacobi_apply(sts_dd_t dd, const double *const *x, double *const *z, int trans);
+
+/*
+ * Solve J x = b (or J^T x = b) over the partition by right-preconditioned
+ * restarted GMRES (Section 6, Eq. right_precond_system), the same algorithm as
+ * sts_gmres_solve (classical Gram-Schmidt with a second pass, Givens rotations
+ * on the host in FP64), with one halo exchange per matvec and three sums over
+ * the processes per Arnoldi step (the first and second Gram-Schmidt dot
+ * products, the norm).  b[k], x[k] as in sts_dd_matvec (x: initial guess on
+ * entry, solution on exit; ghost entries ignored on entry, zero on exit).
+ * opts: restart, max_iters, rtol, precond, trans, history; left and mixed are
+ * not supported here (STS_ERR_INVALID_ARG).  Every process must call it with
+ * the same options.  Synchronous.  Errors as sts_gmres_solve, plus STS_ERR_COMM.
+ */
+sts_status sts_dd_gmres_solve(sts_dd_t dd, const double *const *b, double *const *x, const sts_gmres_opts *opts,
+                              sts_gmres_info *info);
+
+sts_status sts_dd_destroy(sts_dd_t dd);
+
+/*
+ * The same GMRES driver over operations supplied by the caller, for a local
+ * operator or a communication layer that this library does not provide (it is
+ * how the driver is tested on CPU ranks).  Vectors are named by index:
+ *   0 .. m          the Krylov basis v_0 .. v_m        (m = opts->restart)
+ *   m+1 .. 2m       the preconditioned vectors z_0 .. z_{m-1}
+ *   2m+1 w, 2m+2 r, 2m+3 x (initial guess on entry, solution on exit), 2m+4 b.
+ * The callbacks act on this process's share of each vector and return 0 on
+ * success (else the driver returns STS_ERR_COMM):
+ *   matvec(in, out)      out = A in, including any halo exchange it needs
+ *   apply(in, out)       out = M in
+ *   copy(out, in), sub(out, a, b): out = a - b, scale(out, in, s): out = s in (s = 0 writes zeros)
+ *   dots(v0, k, w, self, out)    out[i] = v_{v0+i} . w over this process's share,
+ *                        i < k, and out[k] = w . w when self is 1
+ *   update(w, v0, k, h, norm, out)   w -= sum_{i<k} h[i] v_{v0+i}; out[0] = w . w
+ *                        (this process's share) when norm is 1
+ *   norm2(v, out)        out[0] = v . v over this process's share
+ *   axpy(x, v0, k, y)    x += sum_{i<k} y[i] v_{v0+i}
+ *   allreduce(vals, n)   sum over all processes, in place (HOST memory)
+ */
+typedef struct {
+    void *ctx;
+    int (*matvec)(void *ctx, int in, int out);
+    int (*apply)(void *ctx, int in, int out);
+    int (*copy)(void *ctx, int out, int in);
+    int (*sub)(void *ctx, int out, int a, int b);
+    int (*scale)(void *ctx, int out, int in, double s);
+    int (*dots)(void *ctx, int v0, int k, int w, int self, double *out);
+    int (*update)(void *ctx, int w, int v0, int k, const double *h, int norm, double *out);
+    int (*norm2)(void *ctx, int v, double *out);
+    int (*axpy)(void *ctx, int x, int v0, int k, const double *y);
+    int (*allreduce)(void *ctx, double *vals, int count);
+} sts_dd_ops;
+
+sts_status sts_dd_gmres_ops(const sts_dd_ops *ops, const sts_gmres_opts *opts, sts_gmres_info *info);
 
 /* ---------------------------------------------------------------------------
  * Jacobian generator of a toy flow model: the first-order finite-volume

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsts.so")
 STS_OK = 0
 STATUS_NAMES = {0: "STS_OK", 1: "STS_ERR_INVALID_ARG", 2: "STS_ERR_ALLOC", 3: "STS_ERR_CUDA",
                 4: "STS_ERR_SINGULAR", 5: "STS_ERR_NOT_CONVERGED", 6: "STS_ERR_NUMERIC",
-                7: "STS_ERR_TIMEOUT", 8: "STS_ERR_NOT_SETUP"}
+                7: "STS_ERR_TIMEOUT", 8: "STS_ERR_NOT_SETUP", 9: "STS_ERR_COMM"}
 STS_F64, STS_MIXED = 0, 2
 STS_LAYOUT_CELL_MAJOR, STS_LAYOUT_COMPONENT_MAJOR = 0, 1
 STS_REP_FACTORED, STS_REP_DENSE_BSR = 0, 1
@@ -31,7 +31,10 @@ ABI_FUNCTIONS = ["sts_last_error", "sts_version", "sts_jac_create", "sts_jac_upd
                  "sts_jac_bjacobi_apply", "sts_jac_bjacobi_apply_f32", "sts_gmres_solve",
                  "sts_jac_grad", "sts_jac_memory", "sts_launch_count", "sts_selftest_bounded_wait",
                  "sts_jac_destroy", "sts_flow_create", "sts_flow_get_sizes", "sts_flow_get_layout",
-                 "sts_flow_residual", "sts_flow_jacobian", "sts_flow_newton", "sts_flow_destroy"]
+                 "sts_flow_residual", "sts_flow_jacobian", "sts_flow_newton", "sts_flow_destroy",
+                 "sts_dd_plan_create", "sts_dd_plan_sizes", "sts_dd_plan_get", "sts_dd_plan_value_sizes",
+                 "sts_dd_plan_gather", "sts_dd_plan_destroy", "sts_dd_create", "sts_dd_matvec",
+                 "sts_dd_bjacobi_apply", "sts_dd_gmres_solve", "sts_dd_destroy", "sts_dd_gmres_ops"]
 
 
 class sts_jac_desc(ctypes.Structure):
@@ -84,6 +87,43 @@ class sts_gmres_info(ctypes.Structure):
                 ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double)]
 
 
+class sts_dd_sizes(ctypes.Structure):
+    _fields_ = [("n_owned", ctypes.c_int), ("n_ghost", ctypes.c_int), ("n_local", ctypes.c_int),
+                ("nnzb", ctypes.c_int), ("n_neighbors", ctypes.c_int), ("n_send", ctypes.c_int),
+                ("n_recv", ctypes.c_int)]
+
+
+_IP = ctypes.POINTER(ctypes.c_int)
+_DPP = ctypes.POINTER(ctypes.c_void_p)
+DD_EXCHANGE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _IP, _IP, _DPP, _IP, ctypes.c_int,
+                               _IP, _IP, _DPP, _IP, ctypes.c_void_p)
+DD_ALLREDUCE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class sts_dd_comm(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("exchange", DD_EXCHANGE), ("allreduce", DD_ALLREDUCE)]
+
+
+class sts_dd_desc(ctypes.Structure):
+    _fields_ = [("n_parts", ctypes.c_int), ("part_ids", ctypes.c_void_p), ("jac", ctypes.c_void_p),
+                ("plans", ctypes.c_void_p), ("comm", ctypes.POINTER(sts_dd_comm))]
+
+
+_I, _V, _D = ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+DD_OPS_FIELDS = [("matvec", ctypes.CFUNCTYPE(_I, _V, _I, _I)), ("apply", ctypes.CFUNCTYPE(_I, _V, _I, _I)),
+                 ("copy", ctypes.CFUNCTYPE(_I, _V, _I, _I)), ("sub", ctypes.CFUNCTYPE(_I, _V, _I, _I, _I)),
+                 ("scale", ctypes.CFUNCTYPE(_I, _V, _I, _I, ctypes.c_double)),
+                 ("dots", ctypes.CFUNCTYPE(_I, _V, _I, _I, _I, _I, _D)),
+                 ("update", ctypes.CFUNCTYPE(_I, _V, _I, _I, _I, _D, _I, _D)),
+                 ("norm2", ctypes.CFUNCTYPE(_I, _V, _I, _D)),
+                 ("axpy", ctypes.CFUNCTYPE(_I, _V, _I, _I, _I, _D)),
+                 ("allreduce", ctypes.CFUNCTYPE(_I, _V, _D, _I))]
+
+
+class sts_dd_ops(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p)] + DD_OPS_FIELDS
+
+
 class StsError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -131,6 +171,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                 "sts_flow_jacobian": [P, P, P, P, P],
                 "sts_flow_newton": [P, P, P, P, ctypes.POINTER(sts_newton_opts), ctypes.POINTER(sts_newton_info)],
                 "sts_flow_destroy": [P],
+                "sts_dd_plan_create": [I, P, P, I, P, I, ctypes.POINTER(P)],
+                "sts_dd_plan_sizes": [P, ctypes.POINTER(sts_dd_sizes)],
+                "sts_dd_plan_get": [P, P, P, P, P, P, P, P, P, P],
+                "sts_dd_plan_value_sizes": [P, I, I, P, I, I, ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.POINTER(ctypes.c_int), P],
+                "sts_dd_plan_gather": [P, I, I, I, P, I, I, P, P, P, P, P, P, I, P],
+                "sts_dd_plan_destroy": [P],
+                "sts_dd_create": [ctypes.POINTER(sts_dd_desc), ctypes.POINTER(P)],
+                "sts_dd_matvec": [P, P, P, I],
+                "sts_dd_bjacobi_apply": [P, P, P, I],
+                "sts_dd_gmres_solve": [P, P, P, ctypes.POINTER(sts_gmres_opts), ctypes.POINTER(sts_gmres_info)],
+                "sts_dd_destroy": [P],
+                "sts_dd_gmres_ops": [ctypes.POINTER(sts_dd_ops), ctypes.POINTER(sts_gmres_opts),
+                                     ctypes.POINTER(sts_gmres_info)],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)

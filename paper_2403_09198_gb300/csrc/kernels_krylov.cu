@@ -373,6 +373,42 @@ sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
 
 }  // namespace
 
+// Krylov building blocks on one handle's internal vectors of n = b * ncp
+// entries, for the domain-decomposed driver (kernels_dd.cu).  Reductions leave
+// their totals in device memory (out_dev); the caller copies them out.
+sts_status kry_reserve(sts_jac_s *h, int m) { return ensure_workspace(h, m, false); }
+sts_status kry_dots(sts_jac_s *h, const double *V, int k, const double *w, int self, double *out_dev) {
+    Red R{h, (long long)h->b * h->ncp};
+    return R.dots(V, k, w, self, out_dev);
+}
+sts_status kry_update(sts_jac_s *h, double *w, const double *V, int k, const double *hcoef_dev, int norm,
+                      double *out_dev) {
+    Red R{h, (long long)h->b * h->ncp};
+    return R.update(w, V, k, hcoef_dev, norm, out_dev);
+}
+sts_status kry_norm2(sts_jac_s *h, const double *v, double *out_dev) {
+    Red R{h, (long long)h->b * h->ncp};
+    return R.norm2(v, out_dev);
+}
+sts_status kry_sub(sts_jac_s *h, double *r, const double *b, const double *y) {
+    const long long n = (long long)h->b * h->ncp;
+    k_sub<<<grid_for(n, 256), 256, 0, h->stream>>>(r, b, y, n);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+sts_status kry_scale(sts_jac_s *h, double *out, const double *in, double s) {
+    const long long n = (long long)h->b * h->ncp;
+    k_scale<<<grid_for(n, 256), 256, 0, h->stream>>>(out, in, s, n);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+sts_status kry_axpy(sts_jac_s *h, double *x, const double *Z, int k, const double *y_dev) {
+    const long long n = (long long)h->b * h->ncp;
+    k_axpy_multi<double><<<grid_for(n, 256), 256, 0, h->stream>>>(x, Z, n, y_dev, k);
+    STS_LAUNCHED();
+    return STS_OK;
+}
+
 sts_status op_matvec64(sts_jac_s *h, int dir, const double *x, double *y) { return opA64(h, dir, x, y); }
 sts_status op_apply64(sts_jac_s *h, int dir, const double *x, double *z) { return opM64(h, dir, x, z); }
 

@@ -338,6 +338,14 @@ sts_status dense_apply(sts_jac_s *h, const double *x, double *z);
 sts_status op_matvec64(sts_jac_s *h, int dir, const double *x, double *y);
 sts_status op_apply64(sts_jac_s *h, int dir, const double *x, double *z);
 sts_status gmres(sts_jac_s *h, const double *b, double *x, const sts_gmres_opts *o, sts_gmres_info *info);
+sts_status kry_reserve(sts_jac_s *h, int m);
+sts_status kry_dots(sts_jac_s *h, const double *V, int k, const double *w, int self, double *out_dev);
+sts_status kry_update(sts_jac_s *h, double *w, const double *V, int k, const double *hcoef_dev, int norm,
+                      double *out_dev);
+sts_status kry_norm2(sts_jac_s *h, const double *v, double *out_dev);
+sts_status kry_sub(sts_jac_s *h, double *r, const double *b, const double *y);
+sts_status kry_scale(sts_jac_s *h, double *out, const double *in, double s);
+sts_status kry_axpy(sts_jac_s *h, double *x, const double *Z, int k, const double *y_dev);
 
 // kernels_grad.cu
 sts_status grad(sts_jac_s *h, const double *lam, const double *x, double *gS, double *gU, double *gV);
