@@ -70,6 +70,7 @@ enum { STS_F64 = 0, STS_MIXED = 2 };                       /* sts_jac_desc.dtype
 enum { STS_LAYOUT_CELL_MAJOR = 0, STS_LAYOUT_COMPONENT_MAJOR = 1 };
 enum { STS_REP_FACTORED = 0, STS_REP_DENSE_BSR = 1 };      /* sts_jac_desc.representation */
 enum { STS_PRECOND_BJ = 0, STS_PRECOND_NONE = 1 };         /* sts_gmres_opts.precond     */
+enum { STS_ARNOLDI_GRAPH = 0, STS_ARNOLDI_HOST = 1 };      /* sts_gmres_opts.arnoldi     */
 
 typedef struct sts_jac_s *sts_jac_t;
 
@@ -156,6 +157,15 @@ typedef struct {
     double *history;      /* optional host array [max_iters]: rotated residual / ||b|| per step */
     int left;             /* 1: left preconditioning, (M A) x = M b (Section 6, Eq.
                              left_precond_system); needs STS_PRECOND_BJ, not mixed       */
+    int arnoldi;          /* STS_ARNOLDI_GRAPH (default, 0): for right preconditioning in
+                             FP64 with restart <= 64, each cycle's Arnoldi steps run as
+                             one CUDA graph, every step under a conditional node nested
+                             in the previous step's body, which a device-side Givens
+                             kernel switches off once the cycle is done: the host
+                             synchronises once per cycle.  The graph of a (direction,
+                             preconditioning) is built on first use and kept.
+                             STS_ARNOLDI_HOST (1): the host rotates after every step (a
+                             synchronisation per step); left and mixed solves always do */
 } sts_gmres_opts;
 
 /* Result of sts_gmres_solve. */

@@ -68,7 +68,8 @@ class sts_gmres_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("flexible", ctypes.c_int), ("trans", ctypes.c_int),
                 ("mixed", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("vectors_on_host", ctypes.c_int), ("history", ctypes.c_void_p), ("left", ctypes.c_int)]
+                ("vectors_on_host", ctypes.c_int), ("history", ctypes.c_void_p), ("left", ctypes.c_int),
+                ("arnoldi", ctypes.c_int)]
 
 
 class sts_newton_opts(ctypes.Structure):
@@ -337,8 +338,10 @@ class StsJacobian:
     def gmres(self, b, x0=None, *, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1000,
               precond: str = "bj", trans: bool = False, mixed: bool = False,
               inner_rtol: float = 0.0, history: bool = False, raise_on_fail: bool = True,
-              left: bool = False):
-        """Solve J x = b (J^T x = b).  ``b``: CUDA tensor or numpy array (host)."""
+              left: bool = False, graph: bool = True):
+        """Solve J x = b (J^T x = b).  ``b``: CUDA tensor or numpy array (host).
+        ``graph=False`` rotates on the host after every Arnoldi step instead of
+        running each cycle as one CUDA graph."""
         import torch
         on_host = isinstance(b, np.ndarray)
         if on_host:
@@ -350,6 +353,7 @@ class StsJacobian:
         o.restart, o.max_iters, o.rtol = restart, max_iters, rtol
         o.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
         o.trans, o.mixed, o.inner_rtol, o.left = int(trans), int(mixed), inner_rtol, int(left)
+        o.arnoldi = 0 if graph else 1       # STS_ARNOLDI_GRAPH / STS_ARNOLDI_HOST
         o.vectors_on_host = int(on_host)
         hist = np.zeros(max_iters) if history else None
         o.history = hist.ctypes.data if history else None
@@ -487,7 +491,8 @@ class StsFlow:
 
     def newton(self, jac, Q, Qn, *, max_newton: int = 20, rtol: float = 1e-10, atol: float = 0.0,
                max_halvings: int = 8, gmres_rtol: float = 1e-10, restart: int = 30, gmres_max_iters: int = 1000,
-               precond: str = "bj", left: bool = False, forcing: bool = False, raise_on_fail: bool = True):
+               precond: str = "bj", left: bool = False, forcing: bool = False, raise_on_fail: bool = True,
+               graph: bool = True):
         """One pseudo-time step by Newton's method; Q (CUDA [n_cells, b]) is updated
         in place.  Returns (info dict, history of ||R||)."""
         self._states(Q, Qn)
@@ -496,6 +501,7 @@ class StsFlow:
         o.gmres.restart, o.gmres.max_iters, o.gmres.rtol = restart, gmres_max_iters, gmres_rtol
         o.gmres.precond = STS_PRECOND_BJ if precond == "bj" else STS_PRECOND_NONE
         o.gmres.left = int(left)
+        o.gmres.arnoldi = 0 if graph else 1
         o.forcing = int(forcing)
         hist = np.zeros(max_newton + 1)
         o.history = hist.ctypes.data

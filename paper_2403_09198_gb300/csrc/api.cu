@@ -449,6 +449,13 @@ void free_all(sts_jac_s *h) {
     h->allocs.clear();
     if (h->kry.h_pinned) cudaFreeHost(h->kry.h_pinned);
     h->kry.h_pinned = nullptr;
+    if (h->kry.g_pinned) cudaFreeHost(h->kry.g_pinned);
+    h->kry.g_pinned = nullptr;
+    for (auto &row : h->kry.gexec)
+        for (auto &ge : row) {
+            if (ge) cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
 }
 
 bool layout_ok(int l) { return l == STS_LAYOUT_CELL_MAJOR || l == STS_LAYOUT_COMPONENT_MAJOR; }

@@ -339,6 +339,20 @@ sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
         dev_free(h, K.partial);
         dev_free(h, K.red);
         K.V = K.Z = K.partial = K.red = nullptr;
+        // the cycle graphs hold the old buffers and sizes
+        for (auto &row : K.gexec)
+            for (auto &ge : row) {
+                if (ge) cudaGraphExecDestroy(ge);
+                ge = nullptr;
+            }
+        for (double **g : {&K.gH, &K.gcs, &K.gsn, &K.gg, &K.ghist, &K.gpar}) {
+            dev_free(h, *g);
+            *g = nullptr;
+        }
+        dev_free(h, K.gstate);
+        K.gstate = nullptr;
+        if (K.g_pinned) cudaFreeHost(K.g_pinned);
+        K.g_pinned = nullptr;
         K.Z32 = nullptr;
         K.m = 0;
         STS_TRY(dalloc(h, &K.V, (size_t)(m + 1) * n));
@@ -368,6 +382,167 @@ sts_status ensure_workspace(sts_jac_s *h, int m, bool mixed) {
             STS_TRY(dalloc(h, &K.t32b, n));
         }
     }
+    return STS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One Arnoldi cycle as a CUDA graph.  Step j of the cycle is the body of a
+// conditional (IF) node, nested in step j - 1's body: z_j = M v_j, w = A z_j,
+// the two Gram-Schmidt passes,
+// then k_givens, which folds the new Hessenberg column into the rotations on
+// the device (the host loop's arithmetic, in the same order), records the
+// rotated residual, and switches step j + 1 on or off, and finally v_{j+1} =
+// w / h(j+1, j).  The host launches the graph once per cycle and reads the
+// rotated system back once, instead of synchronising after every step.
+
+// Step j's rotations (one thread).  red: h1 at red[0..], h2 at red[ld..], the
+// squared norm at red[2 ld]; par: stop threshold, history scale, 1 / h(j+1,j)
+// (output), steps allowed; state: steps taken, stop reason (0 none, 1
+// criterion met, 2 NaN or Inf).
+__global__ void k_givens(int j, int m, const double *red, int ld, double *H, double *cs, double *sn, double *g,
+                         double *hist, double *par, int *state, cudaGraphConditionalHandle next, int has_next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double *h1 = red, *h2 = red + ld;
+    const double w0 = sqrt(h1[j + 1]);
+    const double hn = sqrt(red[2 * ld]);
+    bool bad = !isfinite(w0) || !isfinite(hn);
+    for (int i = 0; i <= j; ++i) {
+        H[(size_t)i * m + j] = h1[i] + h2[i];
+        bad = bad || !isfinite(H[(size_t)i * m + j]);
+    }
+    int stop = 0;
+    if (bad) {
+        stop = 2;
+    } else {
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+            H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+            H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+        }
+        const double hjj = H[(size_t)j * m + j];
+        const double den = hypot(hjj, hn);
+        cs[j] = hjj / den;
+        sn[j] = hn / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        hist[j] = fabs(g[j + 1]) * par[1];
+        const bool happy = hn <= 1e-14 * w0;
+        if (happy || fabs(g[j + 1]) <= par[0] || (double)(j + 1) >= par[3]) stop = 1;
+        par[2] = 1.0 / hn;
+    }
+    state[0] = j + 1;
+    state[1] = stop;
+    if (has_next) cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+__global__ void k_scale_dev(double *out, const double *in, const double *s, long long n) {
+    const double f = *s;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = in[e] * f;
+}
+
+// Build (once per restart length, direction, preconditioning and stream) the
+// graph of a whole cycle of m steps.  The kernels of a step are recorded by
+// capturing the ordinary host code on a private stream into the step's body.
+sts_status cycle_graph(sts_jac_s *h, int m, int dir, bool pre) {
+    Krylov &K = h->kry;
+    cudaGraphExec_t &exec = K.gexec[dir][pre ? 1 : 0];
+    if (exec && K.g_m[dir][pre ? 1 : 0] == m && K.g_stream[dir][pre ? 1 : 0] == h->stream) return STS_OK;
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    if (!K.gH) {
+        const size_t M = (size_t)K.m;
+        STS_TRY(dalloc(h, &K.gH, (M + 1) * M));
+        STS_TRY(dalloc(h, &K.gcs, M));
+        STS_TRY(dalloc(h, &K.gsn, M));
+        STS_TRY(dalloc(h, &K.gg, M + 1));
+        STS_TRY(dalloc(h, &K.ghist, M));
+        STS_TRY(dalloc(h, &K.gpar, 4));
+        STS_TRY(dalloc(h, &K.gstate, 2));
+        STS_CK(cudaMallocHost(&K.g_pinned, sizeof(double) * ((M + 1) * M + (M + 1) + M + 8)));
+    }
+    const long long n = (long long)h->b * h->ncp;
+    const int ld = m + 2;
+    cudaGraph_t graph = nullptr;
+    STS_CK(cudaGraphCreate(&graph, 0));
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_error(STS_ERR_CUDA, "gmres graph: cudaStreamCreate failed: %s", cudaGetErrorString(e));
+    }
+    std::vector<cudaGraphConditionalHandle> hd(m);
+    sts_status st = STS_OK;
+    for (int j = 0; j < m && e == cudaSuccess; ++j)
+        e = cudaGraphConditionalHandleCreate(&hd[j], graph, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault);
+    cudaStream_t saved = h->stream;
+    // step j + 1's conditional node sits at the end of step j's body, so once a
+    // step switches the next one off nothing further of the cycle is evaluated
+    cudaGraph_t parent = graph;
+    std::vector<cudaGraphNode_t> deps;
+    Red R{h, n};
+    for (int j = 0; j < m && e == cudaSuccess && st == STS_OK; ++j) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = hd[j];
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddNode(&node, parent, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+        if (e != cudaSuccess) break;
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) break;
+        h->stream = cs;
+        auto step = [&]() -> sts_status {
+            double *vj = K.V + (size_t)j * n, *zj = K.Z + (size_t)j * n;
+            if (pre) STS_TRY(opM64(h, dir, vj, zj));
+            else STS_CK(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, cs));
+            STS_TRY(opA64(h, dir, zj, K.w));
+            double *h1 = K.red, *h2 = K.red + ld, *nr = K.red + 2 * ld;
+            STS_TRY(R.dots(K.V, j + 1, K.w, 1, h1));
+            STS_TRY(R.update(K.w, K.V, j + 1, h1, 0, nullptr));
+            STS_TRY(R.dots(K.V, j + 1, K.w, 0, h2));
+            STS_TRY(R.update(K.w, K.V, j + 1, h2, 1, nr));
+            const int has_next = j + 1 < m ? 1 : 0;
+            k_givens<<<1, 32, 0, cs>>>(j, m, K.red, ld, K.gH, K.gcs, K.gsn, K.gg, K.ghist, K.gpar, K.gstate,
+                                       has_next ? hd[j + 1] : hd[j], has_next);
+            STS_LAUNCHED();
+            if (has_next) {
+                k_scale_dev<<<grid_for(n, 256), 256, 0, cs>>>(K.V + (size_t)(j + 1) * n, K.w, K.gpar + 2, n);
+                STS_LAUNCHED();
+            }
+            return STS_OK;
+        };
+        st = step();
+        h->stream = saved;
+        if (st == STS_OK) {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t *last = nullptr;
+            size_t nlast = 0;
+            e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &last, nullptr, &nlast);
+            if (e == cudaSuccess) deps.assign(last, last + nlast);
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        if (e == cudaSuccess) e = e2;
+        parent = body;
+    }
+    h->stream = saved;
+    if (st == STS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (st != STS_OK) return st;
+    if (e != cudaSuccess) {
+        exec = nullptr;
+        return set_error(STS_ERR_CUDA, "gmres graph: building the cycle graph failed: %s", cudaGetErrorString(e));
+    }
+    K.g_m[dir][pre ? 1 : 0] = m;
+    K.g_stream[dir][pre ? 1 : 0] = h->stream;
     return STS_OK;
 }
 
@@ -424,6 +599,10 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
     const int dir = d.trans ? 1 : 0;
     const bool mixed = d.mixed != 0;
     const bool left = d.left != 0;
+    // graph cycles for right preconditioning in FP64, unless the caller asks for
+    // host-driven steps; restart lengths above 64 keep the host loop (a step's
+    // conditional node is nested in the previous step's body)
+    const bool use_graph = d.arnoldi != STS_ARNOLDI_HOST && !left && !mixed && m <= 64;
     if (left && (!pre || mixed))
         return set_error(STS_ERR_INVALID_ARG, "gmres: left preconditioning needs precond BJ and mixed = 0");
     if (d.precond != STS_PRECOND_BJ && d.precond != STS_PRECOND_NONE)
@@ -506,7 +685,39 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
             std::fill(g.begin(), g.end(), 0.0);
             g[0] = g0;
             int k = 0;
-            for (int j = 0; j < m; ++j) {
+            if (use_graph) {
+                // the whole cycle on the device; one synchronisation to read its rotated system
+                NvtxRange nvtx_graph("gmres cycle graph");
+                STS_TRY(cycle_graph(h, m, dir, pre));
+                double *pp = K.g_pinned;
+                const size_t nH = (size_t)(m + 1) * m;
+                double *pH = pp + 8, *pg = pH + nH, *ph = pg + (m + 1);
+                int *ps = reinterpret_cast<int *>(pp + 4);
+                pp[0] = stop_abs;
+                pp[1] = hscale;
+                pp[2] = 0.0;
+                pp[3] = (double)std::min(m, max_iters - its);
+                for (int i = 0; i <= m; ++i) pg[i] = g[i];
+                STS_CK(cudaMemcpyAsync(K.gpar, pp, sizeof(double) * 4, cudaMemcpyHostToDevice, h->stream));
+                STS_CK(cudaMemcpyAsync(K.gg, pg, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, h->stream));
+                STS_CK(cudaGraphLaunch(K.gexec[dir][pre ? 1 : 0], h->stream));
+                STS_CK(cudaMemcpyAsync(ps, K.gstate, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaMemcpyAsync(pH, K.gH, sizeof(double) * nH, cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaMemcpyAsync(pg, K.gg, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaMemcpyAsync(ph, K.ghist, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaStreamSynchronize(h->stream));
+                k = ps[0];
+                if (ps[1] == 2) {
+                    status = set_error(STS_ERR_NUMERIC, "gmres: NaN or Inf in the Arnoldi process");
+                    break;
+                }
+                std::copy(pH, pH + nH, H.begin());
+                std::copy(pg, pg + (m + 1), g.begin());
+                for (int i = 0; i < k; ++i)
+                    if (d.history && its + i < max_iters) d.history[its + i] = ph[i];
+                its += k;
+            }
+            for (int j = 0; j < m && !use_graph; ++j) {
                 NvtxRange nvtx_step("gmres arnoldi step");
                 double *vj = K.V + (size_t)j * n;
                 // z_j = M v_j, w = A z_j (left: w = M (A v_j))

@@ -241,6 +241,18 @@ struct Krylov {
     double *h_pinned = nullptr;  // host pinned [m+2]
     double *c = nullptr;         // pair dots scratch [n_tiles*n_pslots*32]
     float *c32 = nullptr;
+    // A cycle's Arnoldi steps as one CUDA graph (sts_gmres_opts.arnoldi): the
+    // Givens state lives on the device, sized for m
+    double *gH = nullptr;        // [(m+1) * m] Hessenberg matrix, rotated in place
+    double *gcs = nullptr, *gsn = nullptr;   // [m] rotations
+    double *gg = nullptr;        // [m+1] rotated right-hand side
+    double *ghist = nullptr;     // [m] rotated residual / ||b|| per step
+    double *gpar = nullptr;      // [4] stop threshold, history scale, 1 / h(j+1,j), steps allowed
+    int *gstate = nullptr;       // [2] steps taken, stop reason (1 criterion met, 2 NaN or Inf)
+    double *g_pinned = nullptr;  // host pinned copy of the above
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [direction][preconditioned]
+    int g_m[2][2] = {{0, 0}, {0, 0}};
+    cudaStream_t g_stream[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 }  // namespace sts

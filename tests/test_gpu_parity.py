@@ -223,6 +223,48 @@ def test_gmres_parity(case):
     jac.close()
 
 
+@pytest.mark.parametrize("case", ["bj_restart4", "none_long", "trans", "dense", "max_iters"])
+def test_gmres_cycle_graph(case):
+    """Each cycle as one CUDA graph (device-side Givens rotations, conditional
+    steps; the default): the same iterations and rotated residuals as the
+    host-driven solver, the oracle's solution at rtol 1e-14, and across cycles, the
+    transposed and unpreconditioned solves, dense storage and a step budget
+    that ends inside a cycle."""
+    w = inputs.make_workload(6, 5, N=4, w=2, r_diag=2, r_off=1, seed=9, dt=0.5)
+    J = oracle_jac(w)
+    kw, jkw = dict(restart=4), dict(transpose=True)
+    if case == "none_long":
+        kw = dict(restart=40, precond="none")
+    elif case == "trans":
+        kw = dict(restart=6, trans=True)
+    elif case == "dense":
+        jkw = dict(dense=True)
+    jac = _jac(w, **jkw)
+    jac.bjacobi_setup()
+    if case == "max_iters":
+        xg, ig = jac.gmres(dev(w.rhs), rtol=1e-14, max_iters=6, restart=4, graph=True, history=True,
+                           raise_on_fail=False)
+        xh, ih = jac.gmres(dev(w.rhs), rtol=1e-14, max_iters=6, restart=4, history=True, raise_on_fail=False,
+                           graph=False)
+        assert not ig.converged and ig.iterations == ih.iterations == 6 and ig.restarts == ih.restarts == 2
+        np.testing.assert_allclose(ig.history, ih.history, rtol=1e-12, atol=0)
+        assert sol_err(host(xg), host(xh)) <= 1e-13
+        jac.close()
+        return
+    trans = kw.get("trans", False)
+    xg, ig = jac.gmres(dev(w.rhs), rtol=1e-10, graph=True, history=True, **kw)
+    xh, ih = jac.gmres(dev(w.rhs), rtol=1e-10, history=True, graph=False, **kw)
+    assert ig.converged and ig.iterations == ih.iterations and ig.restarts == ih.restarts
+    np.testing.assert_allclose(ig.history, ih.history, rtol=1e-12, atol=1e-16)
+    r = w.rhs - oracle.matvec(J, host(xg), trans=trans)
+    assert np.linalg.norm(r) / np.linalg.norm(w.rhs) <= 1e-10
+    xg2, i2 = jac.gmres(dev(w.rhs), rtol=1e-14, max_iters=400, graph=True, **kw)
+    xo2, _ = oracle.gmres(J, w.rhs, rtol=1e-14, max_iters=400, precond=kw.get("precond", "bj"), trans=trans,
+                          restart=kw["restart"])
+    assert i2.converged and sol_err(host(xg2), xo2) <= TOL64
+    jac.close()
+
+
 def test_gmres_host_vectors_transposed_and_unpreconditioned():
     w = workload("ragged5x3")
     J = oracle_jac(w)
