@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "ring.cuh"
+#include "smw_stream.cuh"
 #include "sts_internal.h"
 
 namespace sts {
@@ -234,7 +235,7 @@ constexpr int kApStages = 3;    // stages in flight (two ahead of the one consum
 // sweeps run a flat program (one descriptor per stream position).
 template <typename T, int RMAX>
 __global__ void __launch_bounds__(32) k_smw_apply(ApplyArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *stg = reinterpret_cast<T *>(smem_raw);                  // [kApStages][kApStage][32]
     T *w = stg + kApStages * kApStage * kTile;                  // [b][32]
     const int lane = threadIdx.x;
@@ -367,10 +368,6 @@ __host__ __device__ constexpr int sap_rmax(int r, int w) {
 // reports).  Where both fit, the unfolded form measured faster (band 2, two pairs).
 __host__ __device__ constexpr bool sap_fold(int rmax, int w) { return rmax > 2 || w == 1 || w == 4; }
 
-__host__ __device__ constexpr int sap_gcd(int a, int b) { return b == 0 ? a : sap_gcd(b, a % b); }
-// rows per group for rows of `width` positions, VEC positions per vector
-__host__ __device__ constexpr int sap_rows(int width, int vec) { return vec / sap_gcd(width, vec); }
-__host__ __device__ constexpr int sap_round(int n, int vec) { return (n + vec - 1) / vec * vec; }
 // Rows per group: the fewest rows of whole vectors, repeated up to at least 16
 // positions (the per-group bookkeeping is then spread over 16 or more FMAs);
 // forward groups hold at most NF + 1 rows, so that their working-vector reads
@@ -392,71 +389,6 @@ __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
     return (raw + 127) / 128 * 128;
 }
 
-
-// One group of G positions in registers (G / VEC 16-byte loads).
-template <typename T, int G>
-struct Group {
-    using V = typename Vec16<T>::type;
-    static constexpr int VEC = 16 / (int)sizeof(T), NV = G / VEC;
-    static_assert(G % VEC == 0, "a group is whole vectors");
-    V v[NV];
-    __device__ __forceinline__ void load(const T *p) {
-        const V *q = reinterpret_cast<const V *>(p);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = q[j * kTile];
-    }
-    __device__ __forceinline__ T operator[](int k) const { return vel(v[k / VEC], k % VEC); }
-};
-
-// One section of rows (forward level rows, backward level rows or tail) in
-// groups of U rows of G stream positions.  The next group's coefficients and
-// working-vector entries are loaded into registers before the current group
-// is processed.  wsrow(j): working-vector row read for section row j;
-// row(g, w, u, j): computes section row j (row u of group g, working-vector
-// entry w) and returns its result; put(j, v) stores the result of section row
-// j, one row late, when its FP64 FMA has long completed.
-template <typename T, int G, int U, typename RingT, typename WsRow, typename RowF, typename PutF>
-__device__ __forceinline__ void sap_section(RingT &R, const T *wl, int nrows, WsRow wsrow, RowF row, PutF put) {
-    const int ng = (nrows + U - 1) / U, nfull = nrows / U;
-    Group<T, G> gA, gB;
-    T xa[U], xb[U];
-    T carry = T(0);
-    auto load = [&](Group<T, G> &g, T (&xv)[U], int grp) {
-        g.load(R.take(G));
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = wl[wsrow(grp * U + u) * kTile];
-    };
-    auto proc = [&](const Group<T, G> &g, const T (&xv)[U], int grp) {
-        T prev = carry;
-        if (grp < nfull) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const T v = row(g, xv[u], u, grp * U + u);
-                if (u > 0 || grp > 0) put(grp * U + u - 1, prev);
-                prev = v;
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (grp * U + u < nrows) {
-                    const T v = row(g, xv[u], u, grp * U + u);
-                    if (u > 0 || grp > 0) put(grp * U + u - 1, prev);
-                    prev = v;
-                }
-        }
-        carry = prev;
-    };
-    if (nrows <= 0) return;
-    load(gA, xa, 0);
-    for (int grp = 0; grp < ng; grp += 2) {
-        if (grp + 1 < ng) load(gB, xb, grp + 1);
-        proc(gA, xa, grp);
-        if (grp + 1 >= ng) break;
-        if (grp + 2 < ng) load(gA, xa, grp + 2);
-        proc(gB, xb, grp + 1);
-    }
-    put(nrows - 1, carry);
-}
 
 // Consumer warp w of block k takes tiles w * gridDim.x + k, + nc * gridDim.x,
 // ... so that tiles are dealt to SMs round-robin and no sub-partition runs two
@@ -572,7 +504,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
 #pragma unroll
         for (int f = 0; f < NF; ++f) accf[f] = T(0);
         sap_section<T, GF, UF>(
-            R, wl, N, [&](int j) { return min(j, b - 1); },
+            R, N, [&](int j) { return wl[min(j, b - 1) * kTile]; },
             [&](const Group<T, GF> &g, T acc, int u, int) {
 #pragma unroll
                 for (int q = 0; q < W; ++q) acc = fma(-g[u * FW + q], win[q], acc);
@@ -633,7 +565,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
 #pragma unroll
             for (int q = 0; q < W; ++q) xw[q] = T(0);
             sap_section<T, GB, UB>(
-                R, wl, N, [&](int j) { return max(N - 1 - j, 0); },
+                R, N, [&](int j) { return wl[max(N - 1 - j, 0) * kTile]; },
                 [&](const Group<T, GB> &g, T wi, int u, int) {
                     T acc = g[u * BW] * wi;
 #pragma unroll
@@ -670,7 +602,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
             const T *xn = a.x + (size_t)cell + (size_t)nw * kTile;
             T *y = a.y + cell;
             sap_section<T, GT, UT>(
-                R, wl, b, [&](int j) { return min(j, b - 1); },
+                R, b, [&](int j) { return wl[min(j, b - 1) * kTile]; },
                 [&](const Group<T, GT> &g, T val, int u, int) {
 #pragma unroll
                     for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
