@@ -194,6 +194,10 @@ sts_status sts_jac_create(const sts_jac_desc *desc, sts_jac_t *out);
 /*
  * Replace the values S, U, V (same layouts and residency flag as at creation),
  * e.g. after a Newton update.  Invalidates the block-Jacobi setup.  Asynchronous.
+ * With values_on_host = 1 the host arrays are copied through a device staging
+ * buffer that the handle allocates on the first update (or creation) from host
+ * memory and keeps until destroy (it counts in sts_jac_memory); the host arrays
+ * must stay valid until the handle's stream has finished the copies.
  */
 sts_status sts_jac_update_values(sts_jac_t h, const double *S, const double *U,
                                  const double *V, int values_on_host);

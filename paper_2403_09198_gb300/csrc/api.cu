@@ -414,14 +414,13 @@ sts_status build_grad_tables(sts_jac_s *h) {
 
 sts_status load_values(sts_jac_s *h, const double *S, const double *U, const double *V, int on_host) {
     const double *dS = S, *dU = U, *dV = V;
-    double *tmp = nullptr;
     const size_t nS = (size_t)h->nnz_S, nP = (size_t)h->n_pairs * h->b;
     if (on_host) {
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), (nS + 2 * nP + 1) * sizeof(double), h->stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(STS_ERR_ALLOC, "staging buffer for host values: %s", cudaGetErrorString(e));
-        }
+        // one staging buffer per handle, allocated on the first update from host
+        // memory and kept: a fresh allocation per update would map and unmap the
+        // whole value array every time
+        if (!h->staging) STS_TRY(dalloc(h, &h->staging, nS + 2 * nP + 1));
+        double *tmp = h->staging;
         STS_CK(cudaMemcpyAsync(tmp, S, nS * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         if (nP) {
             STS_CK(cudaMemcpyAsync(tmp + nS, U, nP * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -440,7 +439,6 @@ sts_status load_values(sts_jac_s *h, const double *S, const double *U, const dou
     } else {
         st = dense_build(h, dS, dU, dV);
     }
-    if (tmp) cudaFreeAsync(tmp, h->stream);
     return st;
 }
 

@@ -291,6 +291,7 @@ struct sts_jac_s {
     sts::DenseRep dense;
     sts::Krylov kry;
     double *vin = nullptr, *vout = nullptr;     // [b*ncp] layout conversion buffers
+    double *staging = nullptr;                  // device copy of host values (first host update on)
     float *vin32 = nullptr, *vout32 = nullptr;
     double *c64 = nullptr;                      // matvec pair dots [n_tiles*n_pslots_max*32]
     int *d_err = nullptr;                       // device: set when a bounded device wait gave up
