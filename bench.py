@@ -289,6 +289,9 @@ def run_ours(args):
     value = ops_done * ws / elapsed
     mv_ms = statistics.median(per["mv"])
     ap_ms = statistics.median(per["ap"])
+    # handle memory of the device-resident step, before the end-to-end leg adds the
+    # staging buffer for values updated from host memory
+    fact_mem = jac.memory_bytes()
 
     # roofline of the dominant operation (one sts_jac_matvec = pair-dot pass + main pass)
     hbm_peak, sm_max_mhz, peak_kind = _peaks()
@@ -380,7 +383,7 @@ def run_ours(args):
                  "factored_setup_ms": 1e3 * fsetup, "factored_gmres_ms": 1e3 * fgm,
                  "factored_gmres_true_rel_residual": finfo.true_rel_residual,
                  "speedup_gmres_time_to_tolerance": dgm / fgm,
-                 "factored_memory_GB": jac.memory_bytes() / 1e9}
+                 "factored_memory_GB": fact_mem / 1e9}
         jd.close()
 
     cpu = None

@@ -329,6 +329,14 @@ def test_values_from_host_memory():
     jac.update_values(w.S * 2.0, w.U, w.V)
     J2 = oracle_jac(w, S=w.S * 2.0)
     assert rel_err(host(jac.matvec(dev(x))), oracle.matvec(J2, x)) <= TOL64
+    # device values in between, then host values again: the staging buffer
+    # kept by the handle is reused and every update lands
+    jac.update_values(dev(w.S), dev(w.U), dev(w.V))
+    assert rel_err(host(jac.matvec(dev(x))), oracle.matvec(J, x)) <= TOL64
+    jac.update_values(w.S * 3.0, w.U * 0.5, w.V)
+    J3 = oracle_jac(w, S=w.S * 3.0, U=w.U * 0.5)
+    for trans in (False, True):
+        assert rel_err(host(jac.matvec(dev(x), trans=trans)), oracle.matvec(J3, x, trans=trans)) <= TOL64
     jac.close()
 
 
