@@ -318,6 +318,57 @@ def test_gmres_nan_is_reported():
     jac.close()
 
 
+def _subset_blocks(w, keep):
+    """The workload restricted to the blocks where ``keep`` is True (diagonal
+    blocks always kept), with their S values and pairs in the same order."""
+    import dataclasses
+    keep = np.asarray(keep) | w.is_diag_block()
+    ks = np.flatnonzero(keep)
+    so, pi = w.s_offsets(), w.pair_indptr.astype(np.int64)
+    rows = np.repeat(np.arange(w.n_cells), np.diff(w.block_indptr))
+    block_indptr = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=w.n_cells))])
+    pair_indptr = np.concatenate([[0], np.cumsum(np.diff(pi)[keep])])
+    return dataclasses.replace(
+        w, block_indptr=block_indptr.astype(np.int32), block_indices=w.block_indices[keep].copy(),
+        pair_indptr=pair_indptr.astype(np.int32),
+        S=np.concatenate([w.S[so[k]:so[k + 1]] for k in ks]),
+        U=np.concatenate([w.U[pi[k]:pi[k + 1]] for k in ks]),
+        V=np.concatenate([w.V[pi[k]:pi[k + 1]] for k in ks]))
+
+
+@pytest.mark.parametrize("layout", ["cell", "component"])
+def test_non_symmetric_block_pattern(layout):
+    """A block pattern that is not symmetric: every row keeps its diagonal and
+    its lower neighbours, one interior cell keeps its whole row.  The widest
+    row then holds 5 blocks and the widest column 4, so the forward and the
+    transposed plans get different slot counts (and kernel instances).  J x,
+    J^T x, the block-Jacobi applies and GMRES in both directions against the
+    oracle."""
+    w0 = inputs.make_workload(7, 6, N=12, w=2, r_diag=2, r_off=1, seed=21)
+    rows = np.repeat(np.arange(w0.n_cells), np.diff(w0.block_indptr))
+    c = 3 * 7 + 3
+    w = _subset_blocks(w0, (w0.block_indices < rows) | (rows == c))
+    counts_r = np.diff(w.block_indptr)
+    counts_c = np.bincount(w.block_indices, minlength=w.n_cells)
+    assert counts_r.max() == 5 and counts_c.max() == 4
+    J = oracle_jac(w)
+    F = oracle.bj_setup(J)
+    jac = _jac(w, transpose=True, layout=layout)
+    jac.bjacobi_setup()
+    cm = (lambda v: to_component_major(v, w.n_cells, w.b)) if layout == "component" else (lambda v: v)
+    cc = (lambda v: from_component_major(v, w.n_cells, w.b)) if layout == "component" else (lambda v: v)
+    x = np.random.default_rng(5).standard_normal(w.n)
+    for trans in (False, True):
+        assert rel_err(cc(host(jac.matvec(dev(cm(x)), trans=trans))), oracle.matvec(J, x, trans=trans)) <= TOL64
+        assert rel_err(cc(host(jac.bjacobi_apply(dev(cm(x)), trans=trans))),
+                       oracle.bj_apply(F, x, trans=trans)) <= TOL64
+        xs, info = jac.gmres(dev(cm(w.rhs)), rtol=1e-14, trans=trans)
+        xo, io = oracle.gmres(J, w.rhs, rtol=1e-14, trans=trans)
+        assert info.converged and abs(info.iterations - io["iterations"]) <= 1
+        assert sol_err(cc(host(xs)), xo) <= TOL64
+    jac.close()
+
+
 def test_values_from_host_memory():
     """Values handed over in host memory (values_on_host = 1) give the same operator."""
     w = workload("grid16_N10")
