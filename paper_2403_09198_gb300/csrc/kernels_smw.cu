@@ -381,9 +381,9 @@ __host__ __device__ constexpr int sap_fwd_rows(int width, int vec, int nf) {
                                                    (nf + 1) % sap_rows(width, vec));
 }
 // shared memory of one consumer warp: stages, 128 bytes of mbarriers (full,
-// empty), working vector [b][32]
+// empty, the first tile's x), working vector [b][32]
 constexpr int kSApBarBytes = 128;
-static_assert(2 * 8 * kSApStages <= kSApBarBytes, "full and empty barriers fit");
+static_assert((2 * kSApStages + 1) * 8 <= kSApBarBytes, "full, empty and x barriers fit");
 __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
     const size_t raw = (size_t)kSApStages * kSApChunkBytes + kSApBarBytes + (size_t)b * kTile * elem;
     return (raw + 127) / 128 * 128;
@@ -428,6 +428,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                 mbar_init(full + 8u * st, 1);
                 mbar_init(full + 8u * (kSApStages + st), 32);
             }
+            mbar_init(full + 8u * (2 * kSApStages), 1);     // the first tile's x
         }
         mbar_init_fence();
     }
@@ -480,8 +481,15 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     R.start(reinterpret_cast<T *>(mine), full, full + 8u * kSApStages, lane);
     pdl_wait();
     pdl_trigger();
-    for (int i = 0; i < b; ++i) cp_async_elem(wl + i * kTile, a.x + i * P + (size_t)gw * kTile + lane);
-    cp_async_commit();
+    // The first tile's x: one bulk copy per row (rows lane, lane + 32, ...),
+    // completed on the warp's x barrier.  Per-lane cp.async of the b rows
+    // measured slower: their issue stalls once the SM's outstanding loads fill.
+    const uint32_t xbar = full + 8u * (2 * kSApStages);
+    if (lane == 0) mbar_expect_tx(xbar, (uint32_t)((size_t)b * kTile * sizeof(T)));
+    __syncwarp();
+    for (int i = lane; i < b; i += kTile)
+        bulk_copy_g2s(smem_addr(wl - lane + (size_t)i * kTile), a.x + (size_t)i * P + (size_t)gw * kTile,
+                      (uint32_t)(kTile * sizeof(T)), xbar);
     for (int k = 0; k < my; ++k) {
         const int cell = (gw + k * nw) * kTile + lane;
         double cz[FOLD ? 1 : RMAX * RMAX];      // C^-1 (transposed for A^T), zero outside r x r
@@ -494,7 +502,11 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                         (i < r && l < r) ? __ldg(a.Cinv + (a.trans ? (size_t)l * r + i : (size_t)i * r + l) * P + cell)
                                          : 0.0;
         }
-        cp_async_wait<0>();
+        if (k == 0) {
+            if (!mbar_wait_bounded(xbar, 0)) goto fail;
+        } else {
+            cp_async_wait<0>();                 // copied in by the previous tile's tail
+        }
         __syncwarp();
         // ---- forward sweep over the level rows: row i = [W band, oldest first | NF flow]
         T win[W > 0 ? W : 1];
@@ -598,29 +610,39 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                     z[i] = (T)sacc;
                 }
             }
-            const bool more = k + 1 < my;
             const T *xn = a.x + (size_t)cell + (size_t)nw * kTile;
             T *y = a.y + cell;
+            // the next tile's x is copied in one group of rows at a time, at
+            // the group's last row (all its rows have been read by then): a
+            // test of the runtime flag on every row measured about 25 cycles
+            // a row even when never taken
+            const bool more = k + 1 < my;
             sap_section<T, GT, UT>(
                 R, b, [&](int j) { return wl[min(j, b - 1) * kTile]; },
-                [&](const Group<T, GT> &g, T val, int u, int) {
+                [&](const Group<T, GT> &g, T val, int u, int j) {
 #pragma unroll
                     for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
+                    if (u == UT - 1 && more) {
+#pragma unroll
+                        for (int q = 0; q < UT; ++q) cp_async_elem(wl + (j - q) * kTile, xn + (size_t)(j - q) * P);
+                    }
                     return val;
                 },
-                [&](int j, T v) {
-                    y[(size_t)j * P] = v;
-                    if (more) cp_async_elem(wl + j * kTile, xn + (size_t)j * P);
-                });
-            cp_async_commit();
+                [&](int j, T v) { y[(size_t)j * P] = v; });
+            if (more) {
+                for (int j = b / UT * UT; j < b; ++j) cp_async_elem(wl + j * kTile, xn + (size_t)j * P);  // ragged last group
+                cp_async_commit();
+            }
         }
         if (R.failed) goto fail;
         R.end_segment();
     }
     return;
 fail:
-    // the producer waits (bounded) for every copy it issued before it exits
+    // the producer waits (bounded) for every copy it issued before it exits;
+    // this warp waits (bounded) for its own copies of the first tile's x
     if (lane == 0) atomicExch(a.err, 1);
+    mbar_wait_bounded(xbar, 0);
     cp_async_wait<0>();
 }
 
