@@ -554,7 +554,9 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
         if ((st = dalloc(h, &h->vin, n)) != STS_OK) break;
         if ((st = dalloc(h, &h->vout, n)) != STS_OK) break;
         if ((st = dalloc(h, &h->d_err, 1)) != STS_OK) break;
-        if (cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) {
+        if ((st = dalloc(h, &h->d_sched, 2)) != STS_OK) break;
+        if (cudaMemsetAsync(h->d_sched, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess) {
             st = set_error(STS_ERR_CUDA, "sts_jac_create: cudaMemsetAsync failed");
             break;
         }
@@ -630,6 +632,7 @@ sts_status check_device(sts_jac_s *h) {
     STS_CK(cudaStreamSynchronize(h->stream));
     if (!flag) return STS_OK;
     STS_CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    if (h->d_sched) STS_CK(cudaMemsetAsync(h->d_sched, 0, 2 * sizeof(unsigned), h->stream));
     return set_error(STS_ERR_TIMEOUT, "a shared-memory bulk copy did not complete within its time limit; results "
                                       "of the matvecs and applies since the last check are invalid");
 }

@@ -30,6 +30,7 @@ struct MvArgs {
     T *y;                   // [b][ncp]
     T *c;                   // [n_tiles][n_dtasks][32]
     int *err;               // set when a bounded wait gave up
+    unsigned *sched;        // [2] pass-2 item counter and finished warps, zero between launches
     int pre;                // the coefficient streams may be read before the grid-dependency wait
     const int *nbr;         // [n_tiles][n_slots][32]
     const unsigned *slot_mask;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
     }
     __syncwarp();
     uint32_t parity = 0;        // bit sg: parity of the next phase of stage sg to wait for
-    // persistent: warp items (tile, group) are dealt round-robin over the grid
+    // persistent: warp items (tile, group), the first round dealt by warp id
     const long long n_items = (long long)a.n_tiles * a.n_groups;
     const long long wstep = (long long)gridDim.x * (blockDim.x >> 5);
     const long long wid0 = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -258,7 +259,14 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
     }
     pdl_wait();
     pdl_trigger();
-    for (long long wid = wid0; wid < n_items; wid += wstep) {
+    // Each warp's first item is wid0; later items come from a counter, so
+    // that sub-partitions running more warps, or lighter items, take more
+    // (static round-robin dealing left the sub-partitions with four warps
+    // finishing last).  The next ticket is taken at the start of an item and
+    // read at its end, so the atomic's latency is hidden.
+    unsigned ticket = 0;
+    for (long long wid = wid0; wid < n_items; wid = wstep + (long long)__shfl_sync(0xffffffffu, ticket, 0)) {
+    if (lane == 0) ticket = atomicAdd(a.sched, 1u);
     const int t = (int)(wid / a.n_groups), g = (int)(wid % a.n_groups);
     const size_t cell = (size_t)t * kTile + lane;
     const T *__restrict__ cc = a.c + (size_t)t * a.n_dtasks * kTile + lane;
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
                 if (!mbar_wait_bounded(bar + 8u * sq, (parity >> sq) & 1u)) break;
                 parity ^= 1u << sq;
             }
-            return;
+            goto done;
         }
         parity ^= 1u << sg;
 #pragma unroll
@@ -412,6 +420,16 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
         if (p + 2 < p1) issue(p + 2);
     }
     if (p1 > p0) *yp = ylag;
+    }
+done:
+    // the last warp to finish resets the counters for the next launch
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(a.sched + 1, 1u) == (unsigned)(wstep - 1)) {
+            atomicExch(a.sched, 0u);
+            atomicExch(a.sched + 1, 0u);
+        }
     }
 }
 
@@ -524,6 +542,7 @@ MvArgs<T> make_args(sts_jac_s *h, int dir, const T *main, const T *dotv, const T
     a.y = y;
     a.c = c;
     a.err = h->d_err;
+    a.sched = h->d_sched;
     a.pre = h->streams_dirty ? 0 : 1;
     a.nbr = P.nbr;
     a.slot_mask = P.slot_mask;
@@ -567,12 +586,14 @@ void (*mv_struct_kernel(int nreg))(MvArgs<T>) {
     return nreg == 8 ? k_mv_struct<T, WD, 8> : nreg ? k_mv_struct<T, WD, 2 * kStructDuff> : k_mv_struct<T, WD, 0>;
 }
 
-// Level rows per pass-2 item.  The persistent grid deals the n_tiles x (groups +
-// 1) items round-robin to W resident warps, so its last round runs partly full.
-// With few rounds, take the group size of 4..8 rows whose last round is fullest
-// (the plan's size unless another fills strictly more); measured on 128 x 128
-// cells, N = 60: 4 rows (last round 85% full) 109.7 us against 111.0 us at 6
-// rows (65%); with 9 diagonal pairs, 6 rows (70%) 154.6 us against 158.0 us at 4.
+// Level rows per pass-2 item.  The persistent grid runs n_tiles x (groups + 1)
+// items on W resident warps (the first round by warp id, the rest from a
+// counter).  With few rounds, take the group size of 4..8 rows whose last
+// round of W is fullest (the plan's size unless another fills strictly more).
+// Measured on 128 x 128 cells, N = 60, when items were dealt round-robin:
+// 4 rows (last round 85% full) 109.7 us against 111.0 us at 6 rows (65%);
+// with 9 diagonal pairs, 6 rows (70%) 154.6 us against 158.0 us at 4.  With
+// the counter: 4 rows 107.9 us, 5 rows 107.1, 6 rows 110.5, 3 rows 111.0.
 inline int pass2_group_rows(int N, int n_tiles, long long W, int s_plan) {
     auto items = [&](int s) { return (long long)n_tiles * ((N + s - 1) / s + 1); };
     auto fill = [&](int s) {
@@ -624,9 +645,10 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &args) {
         warps = (long long)a.n_tiles * a.n_groups;
         const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
         const long long blocks = std::max(1LL, std::min(need, (long long)resident));
-        // an ordinary launch: with a programmatic early start the persistent
-        // blocks begin at different times during pass 1 and finish unevenly
-        kern<<<(unsigned)blocks, kWarpsPerBlock * kTile, smem, h->stream>>>(a);
+        // programmatic dependent launch: the blocks start, and copy their first
+        // rows, while pass 1 finishes; items are taken from a counter, so
+        // blocks that start late do not finish late
+        STS_CK(launch_pdl(kern, dim3((unsigned)blocks), dim3(kWarpsPerBlock * kTile), smem, h->stream, a));
     } else {
         k_mv_main<T><<<grid, 128, 0, h->stream>>>(a);
     }

@@ -295,6 +295,7 @@ struct sts_jac_s {
     float *vin32 = nullptr, *vout32 = nullptr;
     double *c64 = nullptr;                      // matvec pair dots [n_tiles*n_pslots_max*32]
     int *d_err = nullptr;                       // device: set when a bounded device wait gave up
+    unsigned *d_sched = nullptr;                // device: matvec pass-2 item counter, finished warps
     float *c32 = nullptr;
     double *g_c = nullptr;                      // adjoint: pair dots of the T direction
     int *g_pair_cN = nullptr, *g_pair_cT = nullptr, *g_pair_row = nullptr, *g_pair_col = nullptr;
