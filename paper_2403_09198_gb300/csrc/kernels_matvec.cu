@@ -59,6 +59,8 @@ template <> struct Chunk<float> { static constexpr int CH = 16; };
 // Pass-1 stream loads: FP32 positions in 16-byte vectors of 4 (the FP32
 // kernel is bound by memory instructions), FP64 one position per load (the
 // FP64 kernel is bound by the FP64 pipe, and measured faster so).
+// The stream is read with evict-first (streaming) loads: each call reads it
+// once and it is larger than L2, so the x values the tasks share stay there.
 template <typename T> struct DotVec;
 template <> struct DotVec<double> {
     using type = double;
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
     T xa[CH], xb[CH];
     if (present && a.pre) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + i * kTile);
+        for (int i = 0; i < NV; ++i) va[i] = __ldcs(dv + i * kTile);
     }
     pdl_wait();
     pdl_trigger();
@@ -103,14 +105,14 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
         const size_t ncp = a.ncp;
         if (!a.pre) {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + i * kTile);
+            for (int i = 0; i < NV; ++i) va[i] = __ldcs(dv + i * kTile);
         }
 #pragma unroll
         for (int i = 0; i < CH; ++i) xa[i] = __ldg(xj + (size_t)min(i, bm1) * ncp);
         for (int base = 0; base < a.Lp; base += 2 * CH) {
             if (base + CH < a.Lp) {
 #pragma unroll
-                for (int i = 0; i < NV; ++i) vb[i] = __ldg(dv + ((base + CH) / VEC + i) * kTile);
+                for (int i = 0; i < NV; ++i) vb[i] = __ldcs(dv + ((base + CH) / VEC + i) * kTile);
 #pragma unroll
                 for (int i = 0; i < CH; ++i) xb[i] = __ldg(xj + (size_t)min(base + CH + i, bm1) * ncp);
             }
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(128) k_dots(MvArgs<T> a) {
             if (base + CH >= a.Lp) break;
             if (base + 2 * CH < a.Lp) {
 #pragma unroll
-                for (int i = 0; i < NV; ++i) va[i] = __ldg(dv + ((base + 2 * CH) / VEC + i) * kTile);
+                for (int i = 0; i < NV; ++i) va[i] = __ldcs(dv + ((base + 2 * CH) / VEC + i) * kTile);
 #pragma unroll
                 for (int i = 0; i < CH; ++i) xa[i] = __ldg(xj + (size_t)min(base + 2 * CH + i, bm1) * ncp);
             }
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
             if (lane == 0) {
                 const int sg = (r - q0) & 1;
                 mbar_expect_tx(bar + 8u * sg, row_bytes);
-                bulk_copy_g2s(smem_addr(stage0 + (size_t)sg * RL * kTile), src + (size_t)(r - q0) * RL * kTile,
+                bulk_copy_g2s_stream(smem_addr(stage0 + (size_t)sg * RL * kTile), src + (size_t)(r - q0) * RL * kTile,
                               row_bytes, bar + 8u * sg);
             }
         primed = true;
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
         const int sg = (row - p0) & 1;
         if (lane == 0) {
             mbar_expect_tx(bar + 8u * sg, row_bytes);
-            bulk_copy_g2s(smem_addr(stage0 + (size_t)sg * RL * kTile), src0 + (size_t)(row - p0) * RL * kTile,
+            bulk_copy_g2s_stream(smem_addr(stage0 + (size_t)sg * RL * kTile), src0 + (size_t)(row - p0) * RL * kTile,
                           row_bytes, bar + 8u * sg);
         }
     };
@@ -422,10 +424,13 @@ __global__ void __launch_bounds__(64) k_mv_struct(MvArgs<T> a) {
     if (p1 > p0) *yp = ylag;
     }
 done:
-    // the last warp to finish resets the counters for the next launch
+    // The last warp to finish resets the counters for the next launch.  A
+    // warp counts itself out only after it has used the value its last ticket
+    // returned, so every ticket has been taken when the count completes; no
+    // fence is needed (one measured as a membar stall: it waits for the
+    // warp's output stores).
     __syncwarp();
     if (lane == 0) {
-        __threadfence();
         if (atomicAdd(a.sched + 1, 1u) == (unsigned)(wstep - 1)) {
             atomicExch(a.sched, 0u);
             atomicExch(a.sched + 1, 0u);
