@@ -259,10 +259,10 @@ def run_ours(args):
             per["mv"].append(ev[0].elapsed_time(ev[1]) / ops)
             per["ap"].append(ev[1].elapsed_time(ev[2]) / ops)
         # FP64 operator calls of the step: explicit loops, one J^T and one M^T,
-        # and per FP64 solve (iterations + restarts + 1) matvecs and iterations applies
-        mv = ops + 1 + (i64.iterations + i64.restarts + 1) + (iad.iterations + iad.restarts + 1) \
-            + (imx.restarts + 1)
-        ap = ops + 1 + i64.iterations + iad.iterations
+        # and the FP64 products and applies each solve reports (the mixed solve's
+        # FP32 operators are not counted)
+        mv = ops + 1 + i64.matvecs + iad.matvecs + imx.matvecs
+        ap = ops + 1 + i64.applies + iad.applies + imx.applies
         counted.update(mv=mv, ap=ap, gmres=i64, mixed=imx, adjoint=iad)
         return xs, xm, lam, g
 

@@ -174,6 +174,12 @@ typedef struct {
     int restarts;         /* cycles completed                                      */
     int converged;        /* 1 if the true relative residual reached rtol          */
     double true_rel_residual;  /* ||b - J x|| / ||b||, recomputed in FP64 at the end */
+    int matvecs;          /* FP64 products J x (or J^T x) the solve made: one per
+                             Arnoldi step except in mixed mode, one per
+                             true-residual check except the first when x0 = 0 */
+    int applies;          /* FP64 block-Jacobi applies: one per Arnoldi step
+                             when preconditioned (not in mixed mode), plus one
+                             per cycle with left preconditioning              */
 } sts_gmres_info;
 
 /* Message of the last failed call on this thread ("" if none).  Never NULL. */
@@ -267,7 +273,9 @@ sts_status sts_jac_bjacobi_apply_f32(sts_jac_t h, const float *x, float *z, int 
  * Solve J x = b (or J^T x = b) by restarted right-preconditioned GMRES(m)
  * (Section 6, Eq. right_precond_system; Saad & Schultz), classical Gram-Schmidt
  * with a second pass, Givens rotations on the host in FP64.  x holds the
- * initial guess on entry and the solution on exit (pass zeros for x0 = 0).
+ * initial guess on entry and the solution on exit (pass zeros for x0 = 0).  A
+ * zero guess (||x0|| = 0, found in the same pass as ||b||) starts from r = b
+ * without the product J x0.
  * Left preconditioning (opts.left, Eq. left_precond_system): each cycle starts
  * from z = M (b - J x), the Arnoldi operator is M J, x += V y, and a cycle stops
  * once |g| has fallen below ||z|| times the factor rtol ||b|| / ||b - J x|| that

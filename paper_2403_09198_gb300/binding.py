@@ -85,7 +85,8 @@ class sts_newton_info(ctypes.Structure):
 
 class sts_gmres_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
+                ("matvecs", ctypes.c_int), ("applies", ctypes.c_int)]
 
 
 class sts_dd_sizes(ctypes.Structure):
@@ -228,6 +229,14 @@ class GmresInfo:
     converged: bool
     true_rel_residual: float
     history: np.ndarray | None = None
+    matvecs: int = 0          # FP64 J x products the solve made
+    applies: int = 0          # FP64 block-Jacobi applies the solve made
+
+
+def gmres_info(info, hist=None) -> GmresInfo:
+    """GmresInfo from an sts_gmres_info (history cut to the iterations taken)."""
+    return GmresInfo(info.iterations, info.restarts, bool(info.converged), info.true_rel_residual,
+                     hist[:info.iterations].copy() if hist is not None else None, info.matvecs, info.applies)
 
 
 class StsJacobian:
@@ -361,9 +370,7 @@ class StsJacobian:
         st = self.lib.sts_gmres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
         if raise_on_fail:
             check(st)
-        gi = GmresInfo(info.iterations, info.restarts, bool(info.converged), info.true_rel_residual,
-                       hist[:info.iterations].copy() if history else None)
-        return x, gi
+        return x, gmres_info(info, hist if history else None)
 
     def grad(self, lam, x):
         """Adjoint outer products (gS, gU, gV) in the public S / U / V layouts."""

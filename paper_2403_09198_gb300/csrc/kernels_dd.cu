@@ -269,12 +269,15 @@ sts_status dd_gmres(DdOps &ops, const DdParams &P, sts_gmres_info *info) {
     const int m = P.m;
     const int VW = 2 * m + 1, VR = 2 * m + 2, VX = 2 * m + 3, VB = 2 * m + 4;
     auto Zi = [&](int j) { return m + 1 + j; };
-    double t[1];
+    // ||b||^2 and ||x0||^2 in one sum: a zero guess starts from r = b without a product
+    double t[2];
     STS_TRY(ops.norm2(VB, t));
-    STS_TRY(ops.allreduce(t, 1));
+    STS_TRY(ops.norm2(VX, t + 1));
+    STS_TRY(ops.allreduce(t, 2));
     const double bnorm = std::sqrt(t[0]);
+    bool zero_guess = t[1] == 0.0;
     if (!std::isfinite(bnorm)) return set_error(STS_ERR_NUMERIC, "dd gmres: right-hand side has NaN or Inf");
-    sts_gmres_info inf{0, 0, 1, 0.0};
+    sts_gmres_info inf{0, 0, 1, 0.0, 0, 0};
     sts_status status = STS_OK;
     if (bnorm == 0.0) {
         STS_TRY(ops.scale(VX, VX, 0.0));
@@ -283,11 +286,18 @@ sts_status dd_gmres(DdOps &ops, const DdParams &P, sts_gmres_info *info) {
         int its = 0;
         for (;;) {
             NvtxRange nvtx_cycle("dd gmres cycle");
-            STS_TRY(ops.matvec(VX, VW));
-            STS_TRY(ops.sub(VR, VB, VW));
-            STS_TRY(ops.norm2(VR, t));
-            STS_TRY(ops.allreduce(t, 1));
-            const double beta = std::sqrt(t[0]);
+            double beta = bnorm;
+            if (zero_guess) {
+                STS_TRY(ops.copy(VR, VB));
+                zero_guess = false;
+            } else {
+                STS_TRY(ops.matvec(VX, VW));
+                ++inf.matvecs;
+                STS_TRY(ops.sub(VR, VB, VW));
+                STS_TRY(ops.norm2(VR, t));
+                STS_TRY(ops.allreduce(t, 1));
+                beta = std::sqrt(t[0]);
+            }
             if (!std::isfinite(beta)) {
                 status = set_error(STS_ERR_NUMERIC, "dd gmres: residual norm is NaN or Inf");
                 break;
@@ -305,6 +315,8 @@ sts_status dd_gmres(DdOps &ops, const DdParams &P, sts_gmres_info *info) {
                 if (P.pre) STS_TRY(ops.apply(j, Zi(j)));
                 else STS_TRY(ops.copy(Zi(j), j));
                 STS_TRY(ops.matvec(Zi(j), VW));
+                ++inf.matvecs;
+                if (P.pre) ++inf.applies;
                 // CGS2: h1 = V^T w (+ w.w), w -= V h1; h2 = V^T w, w -= V h2, ||w||^2
                 STS_TRY(ops.dots(0, j + 1, VW, 1, h1.data()));
                 STS_TRY(ops.allreduce(h1.data(), j + 2));

@@ -635,12 +635,15 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
         STS_TRY(to_internal64(h, x_src, K.xb));
     }
     double *hp = K.h_pinned;
+    // ||b||^2 and ||x0||^2: a zero guess starts from r = b without a product
     STS_TRY(R.norm2(K.bb, K.red));
-    STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    STS_TRY(R.norm2(K.xb, K.red + 1));
+    STS_CK(cudaMemcpyAsync(hp, K.red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     STS_CK(cudaStreamSynchronize(h->stream));
     const double bnorm = std::sqrt(hp[0]);
+    bool zero_guess = hp[1] == 0.0;
     if (!std::isfinite(bnorm)) return set_error(STS_ERR_NUMERIC, "gmres: right-hand side has NaN or Inf");
-    sts_gmres_info inf{0, 0, 1, 0.0};
+    sts_gmres_info inf{0, 0, 1, 0.0, 0, 0};
     sts_status status = STS_OK;
     if (bnorm == 0.0) {
         STS_CK(cudaMemsetAsync(K.xb, 0, n * sizeof(double), h->stream));
@@ -649,14 +652,21 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
         int its = 0;
         for (;;) {
             NvtxRange nvtx_cycle("gmres cycle");
-            // true residual r = b - A x
-            STS_TRY(opA64(h, dir, K.xb, K.w));
-            k_sub<<<nb, 256, 0, h->stream>>>(K.r, K.bb, K.w, n);
-            STS_LAUNCHED();
-            STS_TRY(R.norm2(K.r, K.red));
-            STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-            STS_CK(cudaStreamSynchronize(h->stream));
-            const double beta = std::sqrt(hp[0]);
+            // true residual r = b - A x (r = b exactly for the zero guess)
+            double beta = bnorm;
+            if (zero_guess) {
+                STS_CK(cudaMemcpyAsync(K.r, K.bb, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+                zero_guess = false;
+            } else {
+                STS_TRY(opA64(h, dir, K.xb, K.w));
+                ++inf.matvecs;
+                k_sub<<<nb, 256, 0, h->stream>>>(K.r, K.bb, K.w, n);
+                STS_LAUNCHED();
+                STS_TRY(R.norm2(K.r, K.red));
+                STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+                STS_CK(cudaStreamSynchronize(h->stream));
+                beta = std::sqrt(hp[0]);
+            }
             if (!std::isfinite(beta)) {
                 status = set_error(STS_ERR_NUMERIC, "gmres: residual norm is NaN or Inf");
                 break;
@@ -669,6 +679,7 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
             if (left) {
                 // z = M r; the cycle works on the preconditioned residual
                 STS_TRY(opM64(h, dir, K.r, K.tmp));
+                ++inf.applies;
                 STS_TRY(R.norm2(K.tmp, K.red));
                 STS_CK(cudaMemcpyAsync(hp, K.red, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
                 STS_CK(cudaStreamSynchronize(h->stream));
@@ -716,6 +727,8 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
                 for (int i = 0; i < k; ++i)
                     if (d.history && its + i < max_iters) d.history[its + i] = ph[i];
                 its += k;
+                inf.matvecs += k;
+                if (pre) inf.applies += k;
             }
             for (int j = 0; j < m && !use_graph; ++j) {
                 NvtxRange nvtx_step("gmres arnoldi step");
@@ -724,11 +737,15 @@ sts_status gmres(sts_jac_s *h, const double *b_pub, double *x_pub, const sts_gmr
                 if (left) {
                     STS_TRY(opA64(h, dir, vj, K.tmp));
                     STS_TRY(opM64(h, dir, K.tmp, K.w));
+                    ++inf.matvecs;
+                    ++inf.applies;
                 } else if (!mixed) {
                     double *zj = K.Z + (size_t)j * n;
                     if (pre) STS_TRY(opM64(h, dir, vj, zj));
                     else STS_CK(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
                     STS_TRY(opA64(h, dir, zj, K.w));
+                    ++inf.matvecs;
+                    if (pre) ++inf.applies;
                 } else {
                     float *zj = K.Z32 + (size_t)j * n;
                     k_convert<float, double><<<nb, 256, 0, h->stream>>>(pre ? K.t32a : zj, vj, n);

@@ -13,9 +13,9 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .binding import (DD_ALLREDUCE, DD_EXCHANGE, DD_OPS_FIELDS, STS_PRECOND_BJ, STS_PRECOND_NONE, GmresInfo,
-                      StsJacobian, _ptr, check, load, sts_dd_comm, sts_dd_desc, sts_dd_ops, sts_dd_sizes,
-                      sts_gmres_info, sts_gmres_opts)
+from .binding import (DD_ALLREDUCE, DD_EXCHANGE, DD_OPS_FIELDS, STS_PRECOND_BJ, STS_PRECOND_NONE,
+                      StsJacobian, _ptr, check, gmres_info, load, sts_dd_comm, sts_dd_desc, sts_dd_ops,
+                      sts_dd_sizes, sts_gmres_info, sts_gmres_opts)
 
 
 def grid_partition(Lx: int, Ly: int, px: int, py: int) -> np.ndarray:
@@ -290,8 +290,7 @@ class DdSolver:
         st = self.lib.sts_dd_gmres_solve(self.h, self._arr(bs), self._arr(xs), ctypes.byref(o), ctypes.byref(info))
         if raise_on_fail:
             check(st)
-        return xs, GmresInfo(info.iterations, info.restarts, bool(info.converged), info.true_rel_residual,
-                             hist[:info.iterations].copy() if history else None)
+        return xs, gmres_info(info, hist if history else None)
 
 
 def gmres_ops(ops, *, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1000, precond: str = "bj",
@@ -342,8 +341,7 @@ def gmres_ops(ops, *, restart: int = 30, rtol: float = 1e-10, max_iters: int = 1
     o, hist = _opts(restart, max_iters, rtol, precond, False, history)
     info = sts_gmres_info()
     st = load().sts_dd_gmres_ops(ctypes.byref(st_ops), ctypes.byref(o), ctypes.byref(info))
-    gi = GmresInfo(info.iterations, info.restarts, bool(info.converged), info.true_rel_residual,
-                   hist[:info.iterations].copy() if history else None)
+    gi = gmres_info(info, hist if history else None)
     gi.error = err[0] if err else None
     gi.status = st
     if raise_on_fail and st != 0:

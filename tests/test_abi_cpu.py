@@ -38,7 +38,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header(lib):
     # int fields then pointers: a mismatch would shift the pointers
     assert ctypes.sizeof(binding.sts_jac_desc) == 6 * 4 + 6 * 8 + 2 * 4 + 8 + 3 * 8 + 2 * 4 + 8
-    assert ctypes.sizeof(binding.sts_gmres_info) == 4 * 4 + 8
+    # three ints, the double (8-aligned), then the two operator counts
+    assert ctypes.sizeof(binding.sts_gmres_info) == 4 * 4 + 8 + 2 * 4
+    assert binding.sts_gmres_info.true_rel_residual.offset == 16
+    assert binding.sts_gmres_info.matvecs.offset == 24 and binding.sts_gmres_info.applies.offset == 28
 
 
 def _desc(w, **kw):

@@ -123,6 +123,7 @@ class OracleOps:
         bl = rhs.reshape(w.n_cells, w.b)[P.local_to_global].ravel()
         bl[self.no:] = 0.0
         self.v[2 * m + 4] = bl
+        self.n_mv = self.n_ap = 0
 
     def halo(self, x):
         import torch
@@ -139,6 +140,7 @@ class OracleOps:
             X[P.recv_cells[P.recv_ptr[k]:P.recv_ptr[k + 1]]] = t.numpy().reshape(-1, b)
 
     def matvec(self, i, o):
+        self.n_mv += 1
         x = self.v[i].copy()
         self.halo(x)
         y = oracle.matvec(self.J, x, trans=self.trans)
@@ -146,6 +148,7 @@ class OracleOps:
         self.v[o] = y
 
     def apply(self, i, o):
+        self.n_ap += 1
         z = oracle.bj_apply(self.F, self.v[i], trans=self.trans)
         z[self.no:] = 0.0
         self.v[o] = z
@@ -201,7 +204,8 @@ def _worker(rank, world, port, q, name, trans, die_rank):
         info = ddm.gmres_ops(ops, restart=m, rtol=1e-14, raise_on_fail=False)
         x = ops.v[2 * m + 3][:ops.no].reshape(P.n_owned, w.b)
         q.put((rank, "ok", info.status, info.iterations, info.true_rel_residual,
-               P.local_to_global[:P.n_owned].tolist(), x.tolist()))
+               P.local_to_global[:P.n_owned].tolist(), x.tolist(),
+               (info.matvecs, info.applies, ops.n_mv, ops.n_ap, info.restarts)))
     except Exception as e:                    # pragma: no cover - reported to the test
         q.put((rank, "error", repr(e)))
     finally:
@@ -242,6 +246,12 @@ def test_distributed_gmres_on_two_gloo_ranks_equals_the_oracle(name, trans):
         assert r[2] == 0 and r[4] <= 1e-14
         x[np.array(r[5])] = np.array(r[6])
         assert abs(r[3] - io["iterations"]) <= 1
+        # reported operator calls equal the callbacks made; the zero guess
+        # starts from r = b, so each cycle's residual check but the first costs
+        # a product, and every Arnoldi step one product and one apply
+        mv, ap, n_mv, n_ap, restarts = r[7]
+        assert (mv, ap) == (n_mv, n_ap)
+        assert mv == r[3] + restarts and ap == r[3]
     assert np.linalg.norm(x.ravel() - xo) <= 1e-12 * np.linalg.norm(xo)
 
 

@@ -318,6 +318,33 @@ def test_gmres_nan_is_reported():
     jac.close()
 
 
+def test_gmres_operator_counts_and_zero_guess():
+    """The solver reports the FP64 products and applies it made.  A zero guess
+    starts from r = b with no product; a nonzero guess costs one more and
+    reaches the oracle's solution too.  Left preconditioning adds one apply per
+    cycle; the mixed solve's inner operators are FP32 and not counted."""
+    w = workload("grid16_N10")
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True, mixed=True)
+    jac.bjacobi_setup()
+    xo, _ = oracle.gmres(J, w.rhs, rtol=1e-14)
+    for graph in (True, False):
+        x, info = jac.gmres(dev(w.rhs), rtol=1e-14, graph=graph)
+        assert info.converged and sol_err(host(x), xo) <= TOL64
+        assert info.matvecs == info.iterations + info.restarts and info.applies == info.iterations
+    x0 = dev(1e-3 * np.random.default_rng(3).standard_normal(w.n))
+    x1, i1 = jac.gmres(dev(w.rhs), x0, rtol=1e-14)
+    assert i1.converged and sol_err(host(x1), xo) <= TOL64
+    assert i1.matvecs == i1.iterations + i1.restarts + 1 and i1.applies == i1.iterations
+    _, il = jac.gmres(dev(w.rhs), rtol=1e-12, left=True)
+    assert il.matvecs == il.iterations + il.restarts and il.applies == il.iterations + il.restarts
+    _, im = jac.gmres(dev(w.rhs), rtol=1e-10, mixed=True)
+    assert im.converged and im.applies == 0 and im.matvecs == im.restarts
+    _, inone = jac.gmres(dev(w.rhs), rtol=1e-12, precond="none")
+    assert inone.applies == 0 and inone.matvecs == inone.iterations + inone.restarts
+    jac.close()
+
+
 def _subset_blocks(w, keep):
     """The workload restricted to the blocks where ``keep`` is True (diagonal
     blocks always kept), with their S values and pairs in the same order."""
