@@ -156,6 +156,34 @@ def test_bjacobi_full_size_sampled(name):
     jac.close()
 
 
+@pytest.mark.parametrize("N", [61, 60])
+def test_bjacobi_two_tiles_per_warp(N):
+    """160 x 160 cells: 800 tiles on 608 apply warps, so 192 warps apply two
+    tiles and copy the second tile's x during the first tile's tail, one row
+    group at a time.  b = 64 fills every tail group (no ragged rows); b = 63
+    leaves a ragged last group, copied after the section.  FP64 in both
+    directions and FP32, on sampled cells against the oracle."""
+    w = inputs.make_workload(160, 160, N=N, w=2, r_diag=2, r_off=1, seed=31)
+    J = oracle_jac(w)
+    jac = _jac(w, transpose=True, mixed=True, layout="component")
+    jac.bjacobi_setup()
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(w.n)
+    # the cells of the tiles that a warp takes second, and of the first tiles
+    cells = np.unique(np.concatenate([np.arange(608 * 32, 609 * 32), np.arange(w.n_cells - 64, w.n_cells),
+                                      np.arange(0, 32), _sample_cells(w, rng)]))
+    xi = dev(to_component_major(x, w.n_cells, w.b))
+    for trans in (False, True):
+        z = from_component_major(host(jac.bjacobi_apply(xi, trans=trans)), w.n_cells, w.b)
+        ref = oracle.bj_cells(J, x, cells, trans=trans)
+        assert rel_err(z.reshape(w.n_cells, w.b)[cells], ref) <= TOL64, trans
+    z32 = host(jac.bjacobi_apply(xi.float())).astype(np.float64)
+    got = from_component_major(z32, w.n_cells, w.b).reshape(w.n_cells, w.b)[cells]
+    ref = oracle.bj_cells(J, x, cells)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+    jac.close()
+
+
 def test_bjacobi_errors():
     w = workload("ragged5x3")
     jac = _jac(w)
