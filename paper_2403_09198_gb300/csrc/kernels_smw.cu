@@ -399,7 +399,15 @@ __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
 // row by row as the tail frees it.  Within a section the next group
 // (coefficients and working-vector entries) is loaded into registers before
 // the current one is used, so the shared-memory latency overlaps the FMAs.
-template <typename T, int W, int RMAX>
+//
+// GW: the working vector lives in y instead of shared memory (the forward
+// sweep reads x from global memory and writes its rows into y; the backward
+// sweep and the tail read and rewrite them in place, loaded a group ahead so
+// the L2 latency overlaps the FMAs).  Chosen where b rows per warp would leave
+// fewer than four consumers per SM (b > 65 in FP64): the ring alone then fits
+// four.  Plain (coherent) loads throughout, since the kernel rewrites the rows
+// it reads and x may be y.
+template <typename T, int W, int RMAX, bool GW>
 __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T> a) {
     constexpr int NF = kStructNF, VEC = 16 / (int)sizeof(T);
     constexpr int K = kSApChunkBytes / (kTile * (int)sizeof(T));
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nc = (int)(blockDim.x >> 5) - 1;                  // consumer warps
-    const size_t wbytes = sap_warp_bytes(a.b, (int)sizeof(T));
+    const size_t wbytes = sap_warp_bytes(GW ? 0 : a.b, (int)sizeof(T));
     const int nw = nc * gridDim.x;
     const int nch = a.Lt / K;
     if (threadIdx.x == 0) {
@@ -485,13 +493,24 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     // completed on the warp's x barrier.  Per-lane cp.async of the b rows
     // measured slower: their issue stalls once the SM's outstanding loads fill.
     const uint32_t xbar = full + 8u * (2 * kSApStages);
-    if (lane == 0) mbar_expect_tx(xbar, (uint32_t)((size_t)b * kTile * sizeof(T)));
-    __syncwarp();
-    for (int i = lane; i < b; i += kTile)
-        bulk_copy_g2s(smem_addr(wl - lane + (size_t)i * kTile), a.x + (size_t)i * P + (size_t)gw * kTile,
-                      (uint32_t)(kTile * sizeof(T)), xbar);
+    if constexpr (!GW) {
+        if (lane == 0) mbar_expect_tx(xbar, (uint32_t)((size_t)b * kTile * sizeof(T)));
+        __syncwarp();
+        for (int i = lane; i < b; i += kTile)
+            bulk_copy_g2s(smem_addr(wl - lane + (size_t)i * kTile), a.x + (size_t)i * P + (size_t)gw * kTile,
+                          (uint32_t)(kTile * sizeof(T)), xbar);
+    }
     for (int k = 0; k < my; ++k) {
         const int cell = (gw + k * nw) * kTile + lane;
+        // row j of the working vector, and row j of this tile's x
+        auto wv = [&](int j) -> T & {
+            if constexpr (GW) return a.y[(size_t)j * P + cell];
+            else return wl[j * kTile];
+        };
+        auto xin = [&](int j) -> T {
+            if constexpr (GW) return a.x[(size_t)j * P + cell];
+            else return wl[j * kTile];
+        };
         double cz[FOLD ? 1 : RMAX * RMAX];      // C^-1 (transposed for A^T), zero outside r x r
         if constexpr (!FOLD) {
 #pragma unroll
@@ -502,12 +521,14 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                         (i < r && l < r) ? __ldg(a.Cinv + (a.trans ? (size_t)l * r + i : (size_t)i * r + l) * P + cell)
                                          : 0.0;
         }
-        if (k == 0) {
-            if (!mbar_wait_bounded(xbar, 0)) goto fail;
-        } else {
-            cp_async_wait<0>();                 // copied in by the previous tile's tail
+        if constexpr (!GW) {
+            if (k == 0) {
+                if (!mbar_wait_bounded(xbar, 0)) goto fail;
+            } else {
+                cp_async_wait<0>();             // copied in by the previous tile's tail
+            }
+            __syncwarp();
         }
-        __syncwarp();
         // ---- forward sweep over the level rows: row i = [W band, oldest first | NF flow]
         T win[W > 0 ? W : 1];
 #pragma unroll
@@ -516,7 +537,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
 #pragma unroll
         for (int f = 0; f < NF; ++f) accf[f] = T(0);
         sap_section<T, GF, UF>(
-            R, N, [&](int j) { return wl[min(j, b - 1) * kTile]; },
+            R, N, [&](int j) { return xin(min(j, b - 1)); },
             [&](const Group<T, GF> &g, T acc, int u, int) {
 #pragma unroll
                 for (int q = 0; q < W; ++q) acc = fma(-g[u * FW + q], win[q], acc);
@@ -527,15 +548,15 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                 if (W > 0) win[W > 0 ? W - 1 : 0] = acc;
                 return acc;
             },
-            [&](int j, T v) { wl[j * kTile] = v; });
+            [&](int j, T v) { wv(j) = v; });
         // ---- forward flow rows: (N+1,N), (N+2,N), (N+2,N+1)
         T wf[NF];
         {
             Group<T, GFF> g;
             g.load(R.take(GFF));
-            wf[0] = wl[N * kTile] - accf[0];
-            wf[1] = fma(-g[0], wf[0], wl[(N + 1) * kTile] - accf[1]);
-            wf[2] = fma(-g[2], wf[1], fma(-g[1], wf[0], wl[(N + 2) * kTile] - accf[2]));
+            wf[0] = xin(N) - accf[0];
+            wf[1] = fma(-g[0], wf[0], xin(N + 1) - accf[1]);
+            wf[2] = fma(-g[2], wf[1], fma(-g[1], wf[0], xin(N + 2) - accf[2]));
         }
         // ---- backward flow rows, with t = V^T x0 accumulated on the way
         T t[RMAX];
@@ -577,7 +598,7 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
 #pragma unroll
             for (int q = 0; q < W; ++q) xw[q] = T(0);
             sap_section<T, GB, UB>(
-                R, N, [&](int j) { return wl[max(N - 1 - j, 0) * kTile]; },
+                R, N, [&](int j) { return wv(max(N - 1 - j, 0)); },
                 [&](const Group<T, GB> &g, T wi, int u, int) {
                     T acc = g[u * BW] * wi;
 #pragma unroll
@@ -591,10 +612,10 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                     if (W > 0) xw[0] = acc;
                     return acc;
                 },
-                [&](int j, T v) { wl[(N - 1 - j) * kTile] = v; });
+                [&](int j, T v) { wv(N - 1 - j) = v; });
         }
 #pragma unroll
-        for (int f = 0; f < NF; ++f) wl[(N + f) * kTile] = xf[f];
+        for (int f = 0; f < NF; ++f) wv(N + f) = xf[f];
         // ---- z = C^-1 t in FP64, then x = x0 - W z (tail row q = W[0..RMAX)[q]);
         //      folded: z = t and tail row q = (W C^-1)[q][0..RMAX)
         {
@@ -618,20 +639,25 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
             // a row even when never taken
             const bool more = k + 1 < my;
             sap_section<T, GT, UT>(
-                R, b, [&](int j) { return wl[min(j, b - 1) * kTile]; },
+                R, b, [&](int j) { return wv(min(j, b - 1)); },
                 [&](const Group<T, GT> &g, T val, int u, int j) {
 #pragma unroll
                     for (int l = 0; l < RMAX; ++l) val = fma(-g[u * RMAX + l], z[l], val);
-                    if (u == UT - 1 && more) {
+                    if constexpr (!GW) {
+                        if (u == UT - 1 && more) {
 #pragma unroll
-                        for (int q = 0; q < UT; ++q) cp_async_elem(wl + (j - q) * kTile, xn + (size_t)(j - q) * P);
+                            for (int q = 0; q < UT; ++q)
+                                cp_async_elem(wl + (j - q) * kTile, xn + (size_t)(j - q) * P);
+                        }
                     }
                     return val;
                 },
                 [&](int j, T v) { y[(size_t)j * P] = v; });
-            if (more) {
-                for (int j = b / UT * UT; j < b; ++j) cp_async_elem(wl + j * kTile, xn + (size_t)j * P);  // ragged last group
-                cp_async_commit();
+            if constexpr (!GW) {
+                if (more) {
+                    for (int j = b / UT * UT; j < b; ++j) cp_async_elem(wl + j * kTile, xn + (size_t)j * P);  // ragged last group
+                    cp_async_commit();
+                }
             }
         }
         if (R.failed) goto fail;
@@ -642,7 +668,7 @@ fail:
     // the producer waits (bounded) for every copy it issued before it exits;
     // this warp waits (bounded) for its own copies of the first tile's x
     if (lane == 0) atomicExch(a.err, 1);
-    mbar_wait_bounded(xbar, 0);
+    if constexpr (!GW) mbar_wait_bounded(xbar, 0);
     cp_async_wait<0>();
 }
 
@@ -1119,10 +1145,14 @@ static sts_status smw_apply_t(sts_jac_s *h, int dir, const T *st, const T *dv, c
     return STS_OK;
 }
 
+template <typename T, int W, bool GW>
+static void (*sap_kernel_gw(int rmax))(SApplyArgs<T>) {
+    return rmax == 2 ? k_smw_sapply<T, W, 2, GW> : rmax == 4 ? k_smw_sapply<T, W, 4, GW>
+                                                              : k_smw_sapply<T, W, sap_rmax_big(W), GW>;
+}
 template <typename T, int W>
-static void (*sap_kernel(int rmax))(SApplyArgs<T>) {
-    return rmax == 2 ? k_smw_sapply<T, W, 2> : rmax == 4 ? k_smw_sapply<T, W, 4>
-                                                          : k_smw_sapply<T, W, sap_rmax_big(W)>;
+static void (*sap_kernel(int rmax, bool gw))(SApplyArgs<T>) {
+    return gw ? sap_kernel_gw<T, W, true>(rmax) : sap_kernel_gw<T, W, false>(rmax);
 }
 
 template <typename T>
@@ -1133,7 +1163,10 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     a.Lt = M.s_lt[sizeof(T) == 8 ? 0 : 1]; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp;
     a.trans = dir; a.n_tiles = h->n_tiles;
     a.pre = h->streams_dirty ? 0 : 1;
-    const size_t per_warp = sap_warp_bytes(h->b, (int)sizeof(T));
+    // the working vector moves to y where b rows per warp would leave fewer
+    // than kApWarps consumers per SM
+    const bool gw = (size_t)(227 * 1024) / sap_warp_bytes(h->b, (int)sizeof(T)) < (size_t)kApWarps;
+    const size_t per_warp = sap_warp_bytes(gw ? 0 : h->b, (int)sizeof(T));
     const int wpb = (int)std::min<size_t>(kApWarps, (size_t)(227 * 1024) / per_warp);
     if (wpb < 1)
         return set_error(STS_ERR_INVALID_ARG, "block size %d needs %zu bytes of shared memory per warp", h->b, per_warp);
@@ -1141,11 +1174,11 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     void (*kern)(SApplyArgs<T>) = nullptr;
     const int rm = sap_rmax(h->r_diag, M.s_w);
     switch (M.s_w) {
-        case 0: kern = sap_kernel<T, 0>(rm); break;
-        case 1: kern = sap_kernel<T, 1>(rm); break;
-        case 2: kern = sap_kernel<T, 2>(rm); break;
-        case 3: kern = sap_kernel<T, 3>(rm); break;
-        default: kern = sap_kernel<T, 4>(rm); break;
+        case 0: kern = sap_kernel<T, 0>(rm, gw); break;
+        case 1: kern = sap_kernel<T, 1>(rm, gw); break;
+        case 2: kern = sap_kernel<T, 2>(rm, gw); break;
+        case 3: kern = sap_kernel<T, 3>(rm, gw); break;
+        default: kern = sap_kernel<T, 4>(rm, gw); break;
     }
     bool &attr = h->sap_attr[sizeof(T) == 8 ? 0 : 1];
     if (!attr && smem > 48 * 1024)
