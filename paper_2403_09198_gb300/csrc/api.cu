@@ -521,7 +521,8 @@ sts_status create_impl(const sts_jac_desc *d, sts_jac_t *out) {
     {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->nsm < 1) {
+            cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->nsm < 1 ||
+            cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
             delete h;
             return set_error(STS_ERR_CUDA, "sts_jac_create: cannot query the device");
         }

@@ -19,6 +19,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "ring.cuh"
@@ -345,6 +346,7 @@ struct SApplyArgs {
     int *err;               // set when a bounded wait gave up
     int Lt, b, N, r, ncp, trans, n_tiles;
     int pre;                // the stream and C^-1 may be read before the grid-dependency wait
+    int evict_first;        // the stream of one call is larger than L2
 };
 
 constexpr int kApWarps = 4;              // consumer warps per block of the structured apply (one per sub-partition)
@@ -444,32 +446,38 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     if (warp == nc) {
         // ---- producer
         if (lane == 0) {
-            RingProducer<T, K, kSApStages, kApWarps> pr;
-            pr.src = a.st;
-            pr.seg_elems = (size_t)a.Lt * kTile;
-            pr.nc = nc;
-            pr.seg_step = nw;
-            pr.nch = nch;
-            pr.maxc = 0;
+            // the L2 policy of the copies is a template argument: a test in the
+            // issue loop slowed the FP32 apply (about 1 us at 128 x 128 cells)
+            auto produce = [&](auto evict_first) {
+                RingProducer<T, K, kSApStages, kApWarps, decltype(evict_first)::value> pr;
+                pr.src = a.st;
+                pr.seg_elems = (size_t)a.Lt * kTile;
+                pr.nc = nc;
+                pr.seg_step = nw;
+                pr.nch = nch;
+                pr.maxc = 0;
 #pragma unroll
-            for (int w = 0; w < kApWarps; ++w) {
-                unsigned char *reg = smem_raw + (size_t)min(w, nc - 1) * wbytes;
-                pr.stg[w] = reinterpret_cast<T *>(reg);
-                pr.full[w] = smem_addr(reg + (size_t)kSApStages * kSApChunkBytes);
-                pr.empty[w] = pr.full[w] + 8u * kSApStages;
-                pr.seg0[w] = w * gridDim.x + blockIdx.x;
-                pr.nseg[w] = (w < nc && pr.seg0[w] < a.n_tiles) ? (a.n_tiles - 1 - pr.seg0[w]) / nw + 1 : 0;
-                pr.issued[w] = 0;
-                pr.pk[w] = 0;
-                pr.pl[w] = 0;
-                pr.maxc = max(pr.maxc, pr.nseg[w] * nch);
-            }
-            bool ok = a.pre ? pr.issue_upto(kSApStages) : true;
-            pdl_wait();
-            pdl_trigger();
-            if (ok) ok = pr.run();
-            if (!ok) atomicExch(a.err, 1);
-            pr.drain();
+                for (int w = 0; w < kApWarps; ++w) {
+                    unsigned char *reg = smem_raw + (size_t)min(w, nc - 1) * wbytes;
+                    pr.stg[w] = reinterpret_cast<T *>(reg);
+                    pr.full[w] = smem_addr(reg + (size_t)kSApStages * kSApChunkBytes);
+                    pr.empty[w] = pr.full[w] + 8u * kSApStages;
+                    pr.seg0[w] = w * gridDim.x + blockIdx.x;
+                    pr.nseg[w] = (w < nc && pr.seg0[w] < a.n_tiles) ? (a.n_tiles - 1 - pr.seg0[w]) / nw + 1 : 0;
+                    pr.issued[w] = 0;
+                    pr.pk[w] = 0;
+                    pr.pl[w] = 0;
+                    pr.maxc = max(pr.maxc, pr.nseg[w] * nch);
+                }
+                bool ok = a.pre ? pr.issue_upto(kSApStages) : true;
+                pdl_wait();
+                pdl_trigger();
+                if (ok) ok = pr.run();
+                if (!ok) atomicExch(a.err, 1);
+                pr.drain();
+            };
+            if (a.evict_first) produce(std::true_type{});
+            else produce(std::false_type{});
         } else {
             pdl_wait();
             pdl_trigger();
@@ -489,16 +497,22 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
     R.start(reinterpret_cast<T *>(mine), full, full + 8u * kSApStages, lane);
     pdl_wait();
     pdl_trigger();
-    // The first tile's x: one bulk copy per row (rows lane, lane + 32, ...),
-    // completed on the warp's x barrier.  Per-lane cp.async of the b rows
-    // measured slower: their issue stalls once the SM's outstanding loads fill.
+    // The first tile's x.  FP64: one bulk copy per row (rows lane, lane + 32,
+    // ...), completed on the warp's x barrier; per-lane cp.async of the b rows
+    // measured slower (their issue stalls once the SM's outstanding loads
+    // fill).  FP32 (128-byte rows): per-lane cp.async measured faster (11.5
+    // against 12.9 us on 128 x 128 cells, N = 60).
+    constexpr bool XBULK = !GW && sizeof(T) == 8;
     const uint32_t xbar = full + 8u * (2 * kSApStages);
-    if constexpr (!GW) {
+    if constexpr (XBULK) {
         if (lane == 0) mbar_expect_tx(xbar, (uint32_t)((size_t)b * kTile * sizeof(T)));
         __syncwarp();
         for (int i = lane; i < b; i += kTile)
             bulk_copy_g2s(smem_addr(wl - lane + (size_t)i * kTile), a.x + (size_t)i * P + (size_t)gw * kTile,
                           (uint32_t)(kTile * sizeof(T)), xbar);
+    } else if constexpr (!GW) {
+        for (int i = 0; i < b; ++i) cp_async_elem(wl + i * kTile, a.x + (size_t)i * P + (size_t)gw * kTile + lane);
+        cp_async_commit();
     }
     for (int k = 0; k < my; ++k) {
         const int cell = (gw + k * nw) * kTile + lane;
@@ -522,10 +536,10 @@ __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T
                                          : 0.0;
         }
         if constexpr (!GW) {
-            if (k == 0) {
+            if (XBULK && k == 0) {
                 if (!mbar_wait_bounded(xbar, 0)) goto fail;
             } else {
-                cp_async_wait<0>();             // copied in by the previous tile's tail
+                cp_async_wait<0>();             // copied in by the previous tile's tail (or, FP32, before it)
             }
             __syncwarp();
         }
@@ -668,7 +682,7 @@ fail:
     // the producer waits (bounded) for every copy it issued before it exits;
     // this warp waits (bounded) for its own copies of the first tile's x
     if (lane == 0) atomicExch(a.err, 1);
-    if constexpr (!GW) mbar_wait_bounded(xbar, 0);
+    if constexpr (XBULK) mbar_wait_bounded(xbar, 0);
     cp_async_wait<0>();
 }
 
@@ -1163,6 +1177,7 @@ static sts_status smw_sapply_t(sts_jac_s *h, int dir, const T *st, const T *x, T
     a.Lt = M.s_lt[sizeof(T) == 8 ? 0 : 1]; a.b = h->b; a.N = h->b - kStructNF; a.r = h->r_diag; a.ncp = h->ncp;
     a.trans = dir; a.n_tiles = h->n_tiles;
     a.pre = h->streams_dirty ? 0 : 1;
+    a.evict_first = (double)a.n_tiles * a.Lt * kTile * sizeof(T) > (double)h->l2_bytes ? 1 : 0;
     // the working vector moves to y where b rows per warp would leave fewer
     // than kApWarps consumers per SM
     const bool gw = (size_t)(227 * 1024) / sap_warp_bytes(h->b, (int)sizeof(T)) < (size_t)kApWarps;

@@ -139,7 +139,9 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
 // call reads once and that are larger than L2: the vectors the call re-reads
 // (x, the pair dots) then stay in L2.  Measured on 128 x 128 cells, N = 60
 // together with streaming loads of the pass-1 coefficients: FP64 matvec 107.0
-// -> 102.6 us, apply 45.7 -> 45.5 us.
+// -> 102.6 us, apply 45.7 -> 45.5 us.  A stream smaller than L2 (the FP32
+// apply's 68.5 MB there) is better copied with the default policy: part of it
+// is still in L2 at the next call.
 __device__ __forceinline__ void bulk_copy_g2s_stream(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
@@ -248,7 +250,8 @@ struct RingConsumer {
 // ring may be issued before the caller's grid-dependency wait (issue_upto),
 // the rest after (run).  At the end it waits for every copy it issued, so none
 // is in flight when its block exits.  Returns false if a wait gave up.
-template <typename T, int K, int S, int NC>
+// EVICT_FIRST: copy with the L2 evict-first hint (streams larger than L2).
+template <typename T, int K, int S, int NC, bool EVICT_FIRST = false>
 struct RingProducer {
     static constexpr uint32_t CB = (uint32_t)K * 32u * (uint32_t)sizeof(T);
     T *stg[NC];
@@ -267,7 +270,8 @@ struct RingProducer {
                 if (c >= S && !mbar_wait_bounded(empty[w] + 8u * s, (uint32_t)(c / S - 1) & 1u)) return false;
                 const T *g = src + (size_t)(seg0[w] + pk[w] * seg_step) * seg_elems + (size_t)pl[w] * K * 32;
                 mbar_expect_tx(full[w] + 8u * s, CB);
-                bulk_copy_g2s_stream(smem_addr(stg[w] + (size_t)s * K * 32), g, CB, full[w] + 8u * s);
+                if constexpr (EVICT_FIRST) bulk_copy_g2s_stream(smem_addr(stg[w] + (size_t)s * K * 32), g, CB, full[w] + 8u * s);
+                else bulk_copy_g2s(smem_addr(stg[w] + (size_t)s * K * 32), g, CB, full[w] + 8u * s);
                 if (++pl[w] == nch) {
                     pl[w] = 0;
                     ++pk[w];

@@ -272,6 +272,7 @@ struct sts_jac_s {
     // launch data computed on first use (per precision: 0 FP64, 1 FP32)
     int device = 0;                     // CUDA device current at creation
     int nsm = 0;                        // SMs of the handle's device
+    int l2_bytes = 0;                   // L2 cache of the handle's device
     struct Resident {                   // resident blocks of one structured pass-2 instance
         const void *kern;
         size_t smem;
