@@ -398,7 +398,7 @@ __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
 // lane 0 issues every bulk copy of the block's rings.  A consumer's tiles form
 // one continuous stream for its ring, so the next tile's first chunks arrive
 // during the current tail; the next tile's x is copied into the working vector
-// row by row as the tail frees it.  Within a section the next group
+// one group of rows at a time as the tail frees it.  Within a section the next group
 // (coefficients and working-vector entries) is loaded into registers before
 // the current one is used, so the shared-memory latency overlaps the FMAs.
 //
@@ -406,9 +406,9 @@ __host__ __device__ inline size_t sap_warp_bytes(int b, int elem) {
 // sweep reads x from global memory and writes its rows into y; the backward
 // sweep and the tail read and rewrite them in place, loaded a group ahead so
 // the L2 latency overlaps the FMAs).  Chosen where b rows per warp would leave
-// fewer than four consumers per SM (b > 65 in FP64): the ring alone then fits
-// four.  Plain (coherent) loads throughout, since the kernel rewrites the rows
-// it reads and x may be y.
+// fewer than four consumers per SM (b > 65 in FP64, b > 131 in FP32): the ring
+// alone then fits four.  Plain (coherent) loads throughout, since the kernel
+// rewrites the rows it reads and x may be y.  wl is then not used.
 template <typename T, int W, int RMAX, bool GW>
 __global__ void __launch_bounds__((kApWarps + 1) * 32) k_smw_sapply(SApplyArgs<T> a) {
     constexpr int NF = kStructNF, VEC = 16 / (int)sizeof(T);
