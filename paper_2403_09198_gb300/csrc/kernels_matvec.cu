@@ -13,6 +13,9 @@
 // same kernels on the transposed plan (S^T patterns, roles of u and v swapped).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include <mutex>
 #include <type_traits>
 
@@ -592,24 +595,20 @@ void (*mv_struct_kernel(int nreg))(MvArgs<T>) {
 }
 
 // Level rows per pass-2 item.  The persistent grid runs n_tiles x (groups + 1)
-// items on W resident warps (the first round by warp id, the rest from a
-// counter).  With few rounds, take the group size of 4..8 rows whose last
-// round of W is fullest (the plan's size unless another fills strictly more).
-// Measured on 128 x 128 cells, N = 60, when items were dealt round-robin:
-// 4 rows (last round 85% full) 109.7 us against 111.0 us at 6 rows (65%);
-// with 9 diagonal pairs, 6 rows (70%) 154.6 us against 158.0 us at 4.  With
-// the counter: 4 rows 107.9 us, 5 rows 107.1, 6 rows 110.5, 3 rows 111.0.
-inline int pass2_group_rows(int N, int n_tiles, long long W, int s_plan) {
-    auto items = [&](int s) { return (long long)n_tiles * ((N + s - 1) / s + 1); };
-    auto fill = [&](int s) {
-        const long long r = items(s) % W;
-        return r == 0 ? 1.0 : (double)r / (double)W;
-    };
-    if (W <= 0 || items(s_plan) >= 8 * W) return s_plan;
-    int best = s_plan;
-    for (int s = 8; s >= 4; --s)
-        if (s <= N && fill(s) > fill(best) + 1e-9) best = s;
-    return best;
+// items on W resident warps: the first round by warp id, the rest from a
+// counter.  With many items per warp the plan's size stands.  With few, the
+// size trades the per-item work (loading the neighbour x values and pair dots
+// and priming the copies: fewer, larger items) against the tail of the last
+// items (smaller items): the best size grows as sqrt(N / s_rl).  Measured at
+// N = 60 (us per FP64 matvec, items of 4 / 5 / 6 / 7 / 8 rows): 128 x 128 cells
+// with s_rl = 30, 102.7 / 102.0 / 106.5 / - / -; with the paper's pair counts
+// (s_rl = 41), 145.0 / 144.8 / 147.5 / 148.5 / 148.2.  The constant puts both
+// at 5 rows.
+inline int pass2_group_rows(int N, int n_tiles, long long W, int s_plan, int s_rl) {
+    const long long items = (long long)n_tiles * ((N + s_plan - 1) / s_plan + 1);
+    if (W <= 0 || items >= 8 * W) return s_plan;
+    const int s = (int)std::lround(3.8 * std::sqrt((double)N / std::max(s_rl, 1)));
+    return std::max(1, std::min({N, 8, std::max(4, s)}));
 }
 
 template <typename T>
@@ -644,7 +643,7 @@ sts_status mv_launch(sts_jac_s *h, const MvArgs<T> &args) {
             resident = std::max(per_sm, 1) * h->nsm;
             h->mvs_resident.push_back({reinterpret_cast<const void *>(kern), smem, resident});
         }
-        a.s_gl = pass2_group_rows(a.sN, a.n_tiles, (long long)resident * kWarpsPerBlock, a.s_gl);
+        a.s_gl = pass2_group_rows(a.sN, a.n_tiles, (long long)resident * kWarpsPerBlock, a.s_gl, a.s_rl);
         a.n_lgroups = (a.sN + a.s_gl - 1) / a.s_gl;
         a.n_groups = a.n_lgroups + 1;
         warps = (long long)a.n_tiles * a.n_groups;
