@@ -89,6 +89,39 @@ def test_subdomain_products_equal_the_global_rows(name, trans):
         assert np.array_equal(zl[:P.n_owned], z.reshape(w.n_cells, w.b)[own])   # per-cell, same arithmetic
 
 
+@pytest.mark.parametrize("px,py", [(2, 2), (3, 1)])
+def test_plans_on_a_non_symmetric_block_pattern(px, py):
+    """A block pattern that is not symmetric (lower neighbours only, plus one
+    full row): a cell is a ghost of a part when it shares a block with an owned
+    cell in either direction, so the owned rows of J x and J^T x still equal the
+    global rows, and the halos agree."""
+    from tests._workloads import nonsymmetric
+    w = nonsymmetric()
+    part = dd.grid_partition(7, 6, px, py)
+    n_parts = px * py
+    J = oracle.Jacobian.from_workload(w)
+    x = np.random.default_rng(4).standard_normal(w.n)
+    plans = [dd.DdPlan(w.block_indptr, w.block_indices, part, n_parts, p) for p in range(n_parts)]
+    owned = np.concatenate([P.local_to_global[:P.n_owned] for P in plans])
+    assert np.array_equal(np.sort(owned), np.arange(w.n_cells))
+    for P in plans:
+        for k, q in enumerate(P.neighbors):
+            Q = plans[q]
+            kq = int(np.where(Q.neighbors == P.part)[0][0])
+            recv = P.local_to_global[P.recv_cells[P.recv_ptr[k]:P.recv_ptr[k + 1]]]
+            sent = Q.local_to_global[Q.send_cells[Q.send_ptr[kq]:Q.send_ptr[kq + 1]]]
+            assert np.array_equal(recv, sent)
+        assert np.array_equal(np.sort(P.recv_cells), np.arange(P.n_owned, P.n_local))
+    for trans in (False, True):
+        y = oracle.matvec(J, x, trans=trans).reshape(w.n_cells, w.b)
+        for P in plans:
+            _, Jl = _local(w, P)
+            xl = x.reshape(w.n_cells, w.b)[P.local_to_global].ravel()
+            yl = oracle.matvec(Jl, xl, trans=trans).reshape(P.n_local, w.b)
+            ref = y[P.local_to_global[:P.n_owned]]
+            assert np.abs(yl[:P.n_owned] - ref).max() <= 1e-13 * np.abs(ref).max(), (P.part, trans)
+
+
 def test_plan_rejects_bad_partitions():
     from paper_2403_09198_gb300.binding import StsError
     w = inputs.make_workload(4, 3, N=2, w=1, seed=0)

@@ -13,6 +13,7 @@ from paper_2403_09198_gb300 import inputs
 from paper_2403_09198_gb300.binding import StsError, StsJacobian
 from tests._gpu import (SMALL, TOL64, dev, from_component_major, full, host, oracle_jac, rel_err,
                         sol_err, to_component_major, workload)
+from tests._workloads import nonsymmetric
 
 pytestmark = pytest.mark.gpu
 
@@ -373,24 +374,6 @@ def test_gmres_operator_counts_and_zero_guess():
     jac.close()
 
 
-def _subset_blocks(w, keep):
-    """The workload restricted to the blocks where ``keep`` is True (diagonal
-    blocks always kept), with their S values and pairs in the same order."""
-    import dataclasses
-    keep = np.asarray(keep) | w.is_diag_block()
-    ks = np.flatnonzero(keep)
-    so, pi = w.s_offsets(), w.pair_indptr.astype(np.int64)
-    rows = np.repeat(np.arange(w.n_cells), np.diff(w.block_indptr))
-    block_indptr = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=w.n_cells))])
-    pair_indptr = np.concatenate([[0], np.cumsum(np.diff(pi)[keep])])
-    return dataclasses.replace(
-        w, block_indptr=block_indptr.astype(np.int32), block_indices=w.block_indices[keep].copy(),
-        pair_indptr=pair_indptr.astype(np.int32),
-        S=np.concatenate([w.S[so[k]:so[k + 1]] for k in ks]),
-        U=np.concatenate([w.U[pi[k]:pi[k + 1]] for k in ks]),
-        V=np.concatenate([w.V[pi[k]:pi[k + 1]] for k in ks]))
-
-
 @pytest.mark.parametrize("layout", ["cell", "component"])
 def test_non_symmetric_block_pattern(layout):
     """A block pattern that is not symmetric: every row keeps its diagonal and
@@ -399,10 +382,7 @@ def test_non_symmetric_block_pattern(layout):
     transposed plans get different slot counts (and kernel instances).  J x,
     J^T x, the block-Jacobi applies and GMRES in both directions against the
     oracle."""
-    w0 = inputs.make_workload(7, 6, N=12, w=2, r_diag=2, r_off=1, seed=21)
-    rows = np.repeat(np.arange(w0.n_cells), np.diff(w0.block_indptr))
-    c = 3 * 7 + 3
-    w = _subset_blocks(w0, (w0.block_indices < rows) | (rows == c))
+    w = nonsymmetric()
     counts_r = np.diff(w.block_indptr)
     counts_c = np.bincount(w.block_indices, minlength=w.n_cells)
     assert counts_r.max() == 5 and counts_c.max() == 4
