@@ -125,3 +125,28 @@ def test_dd_full_size_four_parts():
     S.close()
     for j in jacs:
         j.close()
+
+
+@pytest.mark.parametrize("layout", ["cell", "component"])
+def test_dd_non_symmetric_block_pattern(layout):
+    """A block pattern that is not symmetric, in 2 x 2 parts: J x, J^T x, the
+    block-Jacobi applies and GMRES in both directions against the oracle."""
+    from tests._workloads import nonsymmetric
+    w = nonsymmetric()
+    part = grid_partition(7, 6, 2, 2)
+    J = oracle.Jacobian.from_workload(w)
+    F = oracle.bj_setup(J)
+    plans, jacs, S = _parts(w, part, 4, layout)
+    x = np.random.default_rng(5).standard_normal(w.n)
+    xs = _scatter(w, plans, x, layout)
+    for trans in (False, True):
+        assert rel_err(_gather(w, plans, S.matvec(xs, trans=trans), layout), oracle.matvec(J, x, trans=trans)) <= TOL64
+        assert rel_err(_gather(w, plans, S.bjacobi_apply(xs, trans=trans), layout),
+                       oracle.bj_apply(F, x, trans=trans)) <= TOL64
+        xg, info = S.gmres(_scatter(w, plans, w.rhs, layout), rtol=1e-14, trans=trans)
+        xo, _ = oracle.gmres(J, w.rhs, rtol=1e-14, trans=trans)
+        assert info.converged and sol_err(_gather(w, plans, xg, layout), xo) <= TOL64
+        assert info.matvecs == info.iterations + info.restarts and info.applies == info.iterations
+    S.close()
+    for j in jacs:
+        j.close()
