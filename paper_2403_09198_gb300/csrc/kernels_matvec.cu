@@ -48,8 +48,12 @@ struct MvArgs {
     int sN, s_rl, s_gl, n_lgroups, wd, structured;   // structured layout (see MvPlan)
 };
 
-// Chunk of stream positions held in registers.
-template <typename T> struct Chunk { static constexpr int CH = 8; };
+// Chunk of stream positions held in registers (two chunks in flight per lane).
+// FP64: 4 positions measured faster than 8 (100.6 against 102.2 us per matvec
+// on 128 x 128 cells, N = 60): pass 1 then needs 48 registers instead of 80,
+// and about 10 warps per sub-partition hide the load latency better than 6
+// warps with twice the loads in flight each; 16 took 110.3 us.
+template <typename T> struct Chunk { static constexpr int CH = 4; };
 template <> struct Chunk<float> { static constexpr int CH = 16; };
 
 
