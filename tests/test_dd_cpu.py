@@ -219,7 +219,7 @@ class OracleOps:
         self.comm.allreduce_array(vals)
 
 
-def _worker(rank, world, port, q, name, trans, die_rank):
+def _worker(rank, world, port, q, name, trans, die_rank, guess_rank=-1):
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -232,6 +232,8 @@ def _worker(rank, world, port, q, name, trans, die_rank):
         comm = ddm.TorchComm({p: p for p in range(world)}, device="cpu")
         m = 30
         ops = OracleOps(w, P, comm, m, trans, w.rhs)
+        if rank == guess_rank:             # a nonzero initial guess on this rank's owned rows only
+            ops.v[2 * m + 3][:ops.no] = 1e-3 * np.random.default_rng(rank).standard_normal(ops.no)
         if rank == die_rank:
             os._exit(0)                       # leaves before the solve, nothing in flight
         info = ddm.gmres_ops(ops, restart=m, rtol=1e-14, raise_on_fail=False)
@@ -248,12 +250,13 @@ def _worker(rank, world, port, q, name, trans, die_rank):
             pass
 
 
-def _run(world, name, trans=False, die_rank=-1):
+def _run(world, name, trans=False, die_rank=-1, guess_rank=-1):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, q, name, trans, die_rank)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, name, trans, die_rank, guess_rank))
+             for r in range(world)]
     for p in procs:
         p.start()
     out = []
@@ -292,3 +295,22 @@ def test_killed_rank_makes_the_driver_return_an_error():
     out = _run(2, "tiles2x2", die_rank=1)
     assert len(out) == 1 and out[0][1] == "ok", out
     assert out[0][2] == 9                  # STS_ERR_COMM: the allreduce callback failed, no hang
+
+
+def test_initial_guess_on_one_rank_is_seen_by_all():
+    """A nonzero initial guess on rank 0 only: the zero-guess test sums
+    ||x0||^2 over the ranks, so both ranks compute the initial product (one
+    more than the iterations and restarts) and reach the oracle's solution."""
+    out = _run(2, "tiles2x2", guess_rank=0)
+    assert [r[0] for r in out] == [0, 1] and all(r[1] == "ok" for r in out), out
+    w, _, _ = _case("tiles2x2")
+    J = oracle.Jacobian.from_workload(w)
+    xo, _ = oracle.gmres(J, w.rhs, rtol=1e-14)
+    x = np.zeros((w.n_cells, w.b))
+    for r in out:
+        assert r[2] == 0 and r[4] <= 1e-14
+        x[np.array(r[5])] = np.array(r[6])
+        mv, ap, n_mv, n_ap, restarts = r[7]
+        assert (mv, ap) == (n_mv, n_ap) and mv == r[3] + restarts + 1
+    assert out[0][3] == out[1][3]
+    assert np.linalg.norm(x.ravel() - xo) <= 1e-12 * np.linalg.norm(xo)
