@@ -331,7 +331,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_ops = 0
-        n_e2e = max(1, min(args.steps, 5))
+        n_e2e = max(1, args.steps)
         for _ in range(n_e2e):
             e2e_step()
             e2e_ops += counted["mv"] + counted["ap"]
