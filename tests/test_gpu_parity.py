@@ -157,6 +157,27 @@ def test_bjacobi_full_size_sampled(name):
     jac.close()
 
 
+def test_bjacobi_working_vector_in_y():
+    """b = 143 (N = 140, band +-4, 3 pairs): b rows per warp would leave fewer
+    than four consumers per SM in FP64 and in FP32, so both applies keep their
+    working vector in y.  Every cell against the oracle, both directions in
+    FP64, and the FP32 apply."""
+    w = inputs.make_workload(12, 11, N=140, w=4, r_diag=3, r_off=1, seed=41)
+    J = oracle_jac(w)
+    F = oracle.bj_setup(J)
+    jac = _jac(w, transpose=True, mixed=True, layout="component")
+    jac.bjacobi_setup()
+    x = np.random.default_rng(14).standard_normal(w.n)
+    xi = dev(to_component_major(x, w.n_cells, w.b))
+    for trans in (False, True):
+        z = from_component_major(host(jac.bjacobi_apply(xi, trans=trans)), w.n_cells, w.b)
+        assert rel_err(z, oracle.bj_apply(F, x, trans=trans)) <= TOL64, trans
+    z32 = from_component_major(host(jac.bjacobi_apply(xi.float())).astype(np.float64), w.n_cells, w.b)
+    ref = oracle.bj_apply(F, x)
+    assert np.linalg.norm(z32 - ref) / np.linalg.norm(ref) <= 1e-6
+    jac.close()
+
+
 @pytest.mark.parametrize("N", [61, 60])
 def test_bjacobi_two_tiles_per_warp(N):
     """160 x 160 cells: 800 tiles on 608 apply warps, so 192 warps apply two
